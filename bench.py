@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of the DGDFT hot path on one GB300 (or N replicas under torchrun).
+
+A step is one pass of the whole hot path over the 1024-element graphene-like
+sheet (32 x 32 elements of 16x16x48 points, extended elements 32x32x48, 4096
+atoms, 80-vector filter block, 72 eigenpairs, 64 ALBs): mixed-precision ALB
+generation for every element followed by the interior-penalty DG assembly
+(element + 4 face neighbours).  value = elements / step time.
+
+The JSON line also carries: the roofline of the Chebyshev filter step (timed
+live with CUDA events on its stream), the end-to-end number through the C-ABI
+with host buffers, the FP64 GPU path on a sample of elements, the oracle timed
+on the host cores (a baseline, not the target), SM clocks sampled during the
+timed region and the number of kernel launches.
+
+`--impl reference` times the oracle (the plain FP64 CPU restatement) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ALB elements/sec, mixed vs FP64 at <=1e-6 Ha eigen error; % of roofline"
+UNIT = "elements/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--config", type=int, default=5)
+    ap.add_argument("--degree", type=int, default=40)
+    ap.add_argument("--max-iter", type=int, default=60)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--fp64-elements", type=int, default=64, help="elements in the FP64 GPU sample (0 = skip)")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--elements", type=int, default=0, help="use only the first n elements (smoke runs)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out = ""
+
+    def summary(self):
+        if not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(io.StringIO(self.out)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1])); mx.append(float(row[2])); pw.append(float(row[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, row[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# -------------------------------------------------------------- oracle arm --
+def _oracle_sample(args_tuple):
+    import os as _os
+    _os.environ["OMP_NUM_THREADS"] = "1"
+    _os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    from oracle import driver
+    prob, params, k, max_iter = args_tuple
+    t = time.perf_counter()
+    r = driver.solve_element(prob, params, k, max_iter=max_iter)
+    return time.perf_counter() - t, r["iters"]
+
+
+def oracle_sample(wl, cores, iters_sample, iters_full, degree):
+    """Time the oracle on `cores` elements (one process each) for iters_sample CheFSI iterations.
+
+    Returns (elements/s estimate scaled to iters_full iterations, description)."""
+    import multiprocessing as mp
+    import copy
+    q = copy.copy(wl.params)
+    q.cheb_degree = degree
+    elems = list(range(min(cores, wl.problem.n_elem)))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(len(elems)) as pool:
+        out = pool.map(_oracle_sample, [(wl.problem, q, k, iters_sample) for k in elems])
+    wall = time.perf_counter() - t0
+    per_elem = statistics.mean(t for t, _ in out)
+    # setup (Lanczos + CholQR2 + first Rayleigh-Ritz) ~ one iteration's H applications / degree
+    scale = (iters_full + 1.0) / (iters_sample + 1.0)
+    t_full = per_elem * scale
+    value = len(elems) / t_full
+    desc = (f"{len(elems)} elements of the workload in parallel (one process per core, 1 BLAS/FFT thread), "
+            f"each {iters_sample} CheFSI iterations of degree {degree} (+ start-up); per-element time "
+            f"{per_elem:.1f} s scaled by ({iters_full}+1)/({iters_sample}+1) to a full solve; wall {wall:.1f} s")
+    return value, desc, len(elems)
+
+
+def run_reference(args, wl):
+    cores = os.cpu_count() or 1
+    iters_full = 14  # FP64 CheFSI iterations of a 32x32x48 element at degree 40 (oracle, tol 1e-8)
+    vals = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        v, desc, used = oracle_sample(wl, cores, 1, iters_full, args.degree)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wl.problem.n_elem / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args, wl):
+    p, q = wl.problem, wl.params
+    return {"workload": wl.name, "elements": int(p.n_elem), "atoms": int(p.n_atoms),
+            "q_grid": "x".join(str(int(v)) for v in p.elem_Qn[0]),
+            "e_grid": "x".join(str(int(v)) for v in p.elem_En[0]),
+            "n_blk": int(q.n_blk[0]), "n_eig": int(q.n_eig[0]), "n_alb": int(q.n_alb[0]),
+            "cheb_degree": args.degree, "tol": args.tol, "stencil": int(p.n_stencil), "alpha": wl.alpha,
+            "precision": "mixed (FP32 filter/subspace, FP64 small solves + final FP64 Rayleigh-Ritz)",
+            "l2": "working set >> L2 (blocks 16 GB per FP32 buffer): no flush needed"}
+
+
+# -------------------------------------------------------------- native arm --
+def run_native(args, wl, rank, world, local_rank):
+    import torch
+    from paper_2003_00407_gb300 import api, _abi
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    ctx = api.Context(local_rank)
+    p, q = wl.problem, wl.params
+    M = p.n_elem
+    stream = torch.cuda.current_stream()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step(host=False):
+        res = api.alb_generate(ctx, p, q, precision=_abi.MIXED, cheb_degree=args.degree, tol=args.tol,
+                               max_iter=args.max_iter, keep_eigvec=False, host_buffers=host)
+        blocks = api.dg_assemble_host(ctx, p, q, res, wl.alpha) if host else api.dg_assemble(ctx, p, q, res,
+                                                                                              wl.alpha)
+        return res, blocks
+
+    for _ in range(args.warmup):
+        res, blocks = step()
+    # phase split (one extra untimed-in-value step)
+    barrier()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    res = api.alb_generate(ctx, p, q, precision=_abi.MIXED, cheb_degree=args.degree, tol=args.tol,
+                           max_iter=args.max_iter, keep_eigvec=False)
+    e[1].record(stream)
+    blocks = api.dg_assemble(ctx, p, q, res, wl.alpha)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    t_alb, t_dg = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    iters = res.iters.cpu().numpy()
+    status = res.status.cpu().numpy()
+
+    # ---- timed region ----
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[0] or 0) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local_rank
+    launches0 = ctx.lib.dgdft_kernel_launches()
+    barrier()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_index) as clk:
+        start.record(stream)
+        for _ in range(args.steps):
+            res, blocks = step()
+        stop.record(stream)
+        barrier()
+    launches = ctx.lib.dgdft_kernel_launches() - launches0
+    ms = start.elapsed_time(stop) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * M / (ms / 1000.0)
+
+    # ---- roofline of the Chebyshev step (FP32 filter), timed live on this stream ----
+    roof = filter_roofline(ctx, api, _abi, wl, torch, stream, res)
+
+    # ---- end to end through the C-ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            resh, blocksh = step(host=True)
+        barrier()
+        t_e2e = (time.perf_counter() - t0) / max(1, args.steps)
+        L = resh.L
+        n_alb_pts = int(np.sum(q.n_alb * np.prod(p.elem_En, axis=1)))
+        h2d = 8 * p.v_extra.size * 2 + 8 * M * L * L
+        d2h = 8 * (3 * M * L + M * L * L + n_alb_pts) + 8 * M + 8 * M * p.n_stencil * L * L
+        e2e = {"value": world * M / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # ---- FP64 GPU path on a sample of elements ----
+    fp64 = None
+    if args.fp64_elements > 0:
+        from workloads.configs import subset
+        ns = min(args.fp64_elements, M)
+        ws = subset(wl, range(ns))
+        ws.problem.n_stencil = 1
+        ws.problem.neighbors = np.arange(ns, dtype=np.int32)[:, None].copy()
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        r64 = api.alb_generate(ctx, ws.problem, ws.params, precision=_abi.FP64, cheb_degree=args.degree,
+                               tol=args.tol, max_iter=args.max_iter, keep_eigvec=False)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        t64 = f0.elapsed_time(f1) / 1000.0
+        t_dg_elem = t_dg / 1000.0 / M
+        ev64 = r64.eigval.cpu().numpy()
+        ev32 = res.eigval.cpu().numpy()
+        n_eig = int(q.n_eig[0])
+        diff = float(np.abs(ev64[:ns, :n_eig] - ev32[:ns, :n_eig]).max())
+        fp64 = {"value": ns / (t64 + t_dg_elem * ns), "unit": UNIT,
+                "sample": f"first {ns} elements, FP64 ALB generation timed + DG assembly time per element "
+                          f"of the mixed run (the DG assembly is FP64 in both paths)",
+                "alb_ms": 1000 * t64, "iterations_mean": float(np.mean(r64.iters.cpu().numpy())),
+                "mixed_vs_fp64_max_eig_diff_ha": diff}
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu:
+            iters_full = int(round(np.mean(fp64["iterations_mean"]))) if fp64 else 14
+            v, desc, used = oracle_sample(wl, os.cpu_count() or 1, 1, iters_full, args.degree)
+            cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc}
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config_dict(args, wl),
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+               "clocks": clk.summary(), "fp64_gpu": fp64,
+               "phase_ms": {"alb_generate": t_alb, "dg_assemble": t_dg},
+               "iterations": {"mean": float(iters.mean()), "max": int(iters.max())},
+               "status_nonzero": int(np.count_nonzero(status))}
+    ctx.close()
+    return out
+
+
+def filter_roofline(ctx, api, _abi, wl, torch, stream, res):
+    """Per-degree time of the FP32 Chebyshev step over all elements and vectors, vs HBM bytes."""
+    import copy
+    p, q = wl.problem, wl.params
+    M = p.n_elem
+    N = np.prod(p.elem_Qn, axis=1).astype(np.int64)
+    nb = q.n_blk.astype(np.int64)
+    total = int(np.sum(nb * N))
+    X = torch.randn(total, dtype=torch.float32, device="cuda")
+    ev = res.eigval.cpu().numpy()
+    bounds = np.stack([ev[:, 0], ev[:, int(nb[0]) - 1], np.full(M, 95.0)], axis=1)
+    times = {}
+    for m in (6, 16):
+        api.chebyshev_filter(ctx, p, q, X, bounds, m, precision=_abi.MIXED)  # warm
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        api.chebyshev_filter(ctx, p, q, X, bounds, m, precision=_abi.MIXED)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times[m] = a.elapsed_time(b) / 1000.0
+    t_step = (times[16] - times[6]) / 10.0
+    # algorithmic bytes of one step: read Y_k, read Y_{k-1}, write Y_{k+1} (FP32) + V_eff once per element
+    bytes_step = float(np.sum(12 * N * nb + 4 * N))
+    peak = measured_peak()
+    ach = bytes_step / t_step / 1e9
+    del X
+    return {"bound": "hbm", "achieved": ach, "peak": peak[0], "unit": "GB/s", "frac": ach / peak[0],
+            "traffic": None, "kernel": "Chebyshev step = plane_forward + zline + plane_inverse (FP32)",
+            "step_ms": 1000 * t_step, "bytes_per_step": bytes_step, "peak_source": peak[1]}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    from workloads import make_config
+    from workloads.configs import subset
+    wl = make_config(args.config)
+    if args.elements:
+        wl = subset(wl, range(args.elements))
+        wl.problem.n_stencil = 1
+        wl.problem.neighbors = np.arange(args.elements, dtype=np.int32)[:, None].copy()
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, wl)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    out = run_native(args, wl, rank, world, local_rank)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/* libdgdft: the data-parallel hot path of discontinuous Galerkin DFT
+ * (DGDFT, Sec. II.A of "DGDFT on the Sunway TaihuLight", arXiv 2003.00407)
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ *   dgdft_alb_generate  per-element adaptive local basis: lowest eigenpairs
+ *                       of the local Kohn-Sham Hamiltonian on each extended
+ *                       element Q_k (Eq. LocalKS) by Chebyshev-filtered
+ *                       subspace iteration (Alg. CheFSI), restricted to E_k
+ *                       and truncated by SVD (Sec. II.A.1).
+ *   dgdft_dg_assemble   interior-penalty DG Hamiltonian blocks (Eq.
+ *                       DGHamiltonian) between each element and its stencil
+ *                       neighbours.
+ *   dgdft_alb_grad      Fermi-smeared band energy of the local problems and
+ *                       its Hellmann-Feynman gradient with respect to V_eff
+ *                       and the atom positions (local analogue of Eq. hfforce).
+ *   dgdft_apply_hamiltonian / dgdft_chebyshev_step
+ *                       the hot operator alone (Eq. LocalKS; Alg. CheFSI step 2).
+ *
+ * Conventions
+ *   - Grid functions are stored [z][y][x] (x fastest).  A block of n vectors
+ *     on Q_k is [n][N_k] with N_k = Qx*Qy*Qz.  "Packed" buffers hold the
+ *     blocks of elements 0..M-1 back to back: element k starts after the
+ *     blocks of elements 0..k-1 (sizes from the element's own counts).
+ *   - Problem description arrays (geometry, atoms, counts) are HOST memory,
+ *     read during the call.  Data arrays (v_extra, results, blocks, grads)
+ *     are DEVICE memory owned by the caller unless DGDFT_HOST_BUFFERS is set
+ *     in params.flags, in which case they are host memory and the library
+ *     stages them through its own device workspace (copies inside the call).
+ *   - All calls are ordered on `stream` and synchronise it before returning
+ *     (the iteration count depends on device-side convergence tests).
+ *   - No call traps or aborts: every failure is a status code; the message of
+ *     the last failure is returned by dgdft_last_error.  Device loops are
+ *     bounded by max_iter.
+ *   - A context owns the device workspace (grown on demand, freed by
+ *     dgdft_ctx_destroy) and is not thread safe: use one context per thread.
+ */
+#ifndef DGDFT_H
+#define DGDFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgdft_ctx dgdft_ctx;
+typedef void* dgdft_stream; /* a cudaStream_t; NULL = the legacy default stream */
+
+enum dgdft_status {
+  DGDFT_OK = 0,
+  DGDFT_INVALID_ARG = 1,    /* host-side argument check failed; nothing ran */
+  DGDFT_OUT_OF_MEMORY = 2,  /* workspace allocation failed */
+  DGDFT_NOT_CONVERGED = 3,  /* results written; some element hit max_iter (see status[]) */
+  DGDFT_CHOLESKY_FAIL = 4,  /* Cholesky-QR failed even with a shift (see status[]) */
+  DGDFT_BAD_INPUT = 5,      /* NaN/Inf found in v_extra or produced by the solve */
+  DGDFT_TIMEOUT = 6,        /* reserved: a bounded device wait gave up */
+  DGDFT_CUDA_ERROR = 7,     /* a CUDA call failed; message in dgdft_last_error */
+  DGDFT_UNSUPPORTED = 8     /* valid but outside this build's limits (sizes, radices) */
+};
+
+enum dgdft_precision {
+  DGDFT_FP64 = 0,  /* filter, orthonormalisation and Rayleigh-Ritz in FP64 */
+  DGDFT_MIXED = 1  /* FP32 filter and subspace steps with FP64 small solves,
+                      then one FP64 Rayleigh-Ritz sweep */
+};
+
+enum dgdft_flags {
+  DGDFT_HOST_BUFFERS = 1  /* data arrays are host memory (see Conventions) */
+};
+
+/* Statement of the problem (Sec. II.A: element partition, extended
+ * elements, V_eff, Kleinman-Bylander projectors).  Host memory. */
+typedef struct {
+  int n_dom;                 /* periodic domains (1 for a partitioned system) */
+  const int* dom_n;          /* [n_dom][3] grid points (x, y, z) */
+  const double* dom_h;       /* [n_dom][3] spacing (bohr) */
+  const int64_t* dom_voff;   /* [n_dom] first point of each domain in v_extra / grad_v */
+  const double* v_extra;     /* DATA: V_eff minus the wells on all domains, or NULL (= 0) */
+  int n_elem;                /* M */
+  const int* elem_dom;       /* [M] */
+  const int* elem_E0;        /* [M][3] first grid point of E_k */
+  const int* elem_En;        /* [M][3] extent of E_k */
+  const int* elem_Qn;        /* [M][3] extent of Q_k, centred on E_k (Qn-En even, Qn <= dom_n) */
+  const int* neighbors;      /* [M][n_stencil] element ids; slot 0 = self, then faces
+                                -x,+x,-y,+y(,-z,+z), then (9 slots) xy corners; -1 = none */
+  int n_stencil;             /* 1, 3, 5, 7 or 9 */
+  int n_atoms;
+  const int* atom_dom;       /* [n_atoms] */
+  const double* atom_pos;    /* [n_atoms][3] bohr */
+  const double* well_depth;  /* [n_atoms] D_I: V_I(r) = -D_I exp(-d^2/2w^2) tau(d/r_cut) */
+  const double* well_width;  /* [n_atoms] w_I */
+  int n_proj_per_atom;       /* 0, 1 (s) or 4 (s, px, py, pz) */
+  const double* proj_gamma;  /* [n_atoms][n_proj_per_atom] gamma_{I,l} (Ha) */
+  const double* proj_width;  /* [n_atoms] sigma_I of b = N exp(-d^2/2 sigma^2) tau (p: times d_alpha) */
+  double r_cut;              /* support radius; tau(s) = (1-s^2)^3 for s < 1, each domain side >= 2 r_cut */
+} dgdft_problem;
+
+/* Solver parameters (Alg. CheFSI).  Host memory. */
+typedef struct {
+  const int* n_eig;          /* [M] eigenpairs J_k */
+  const int* n_alb;          /* [M] ALBs kept after the SVD (<= n_eig) */
+  const int* n_blk;          /* [M] filter block (n_eig <= n_blk <= 96), or NULL for the
+                                rule n_eig + max(4, ceil(n_eig/10)) rounded up to 8 */
+  int cheb_degree;           /* filter order m >= 2 */
+  double tol;                /* residual tolerance ||H x - lambda x|| (dV norm) */
+  double tol_mixed;          /* DGDFT_MIXED: the FP32 stage stops at this residual or
+                                when FP32 rounding stalls it; 0 = 1e-6 */
+  int max_iter;              /* cap on filter passes per precision stage */
+  int lanczos_steps;         /* steps of the upper-bound estimate (0 = 10) */
+  int precision;             /* dgdft_precision */
+  uint64_t seed;             /* SplitMix64 state of the random start */
+  int flags;                 /* dgdft_flags */
+} dgdft_alb_params;
+
+/* Results of dgdft_alb_generate (DATA arrays; caller allocated).  Sizes in
+ * scalars from dgdft_alb_query_sizes; L = max_k n_blk padded as returned. */
+typedef struct {
+  double* eigval;   /* [M][L] Ritz values, ascending (first n_blk valid) */
+  double* resid;    /* [M][L] residual norms of the Ritz pairs */
+  double* sing;     /* [M][L] singular values of the restricted block (first n_eig) */
+  double* coef;     /* [M][L][L] C_k: ALB = Phi_E C_k (first n_eig rows, n_alb cols) */
+  double* alb;      /* packed [n_alb][NE] per element: ALB values on E_k, dV-orthonormal */
+  double* eigvec;   /* packed [n_eig][N] per element: eigenvectors on Q_k, dV-orthonormal */
+  int* iters;       /* [M] filter passes (both stages in mixed mode) */
+  int* status;      /* [M] per-element status: 0 ok, or a dgdft_status */
+} dgdft_alb_result;
+
+/* Sizes (in scalars) of the result arrays for a problem:
+ * out[0] = L (row length of eigval/resid/sing and the side of coef),
+ * out[1] = size of alb, out[2] = size of eigvec, out[3] = M*L*L (coef),
+ * out[4] = total points of all domains (grad_v), out[5] = n_stencil*M*L*L (blocks). */
+int dgdft_alb_query_sizes(const dgdft_problem* prob, const dgdft_alb_params* params, int64_t out[6]);
+
+int dgdft_ctx_create(dgdft_ctx** ctx, int device);
+void dgdft_ctx_destroy(dgdft_ctx* ctx);
+/* Message of the last failure on ctx; with ctx == NULL, of the last failure on
+ * this thread that had no context (e.g. dgdft_ctx_create). */
+const char* dgdft_last_error(const dgdft_ctx* ctx);
+
+/* Number of CUDA kernel launches this library has issued since it was loaded
+ * (all contexts, all threads).  For accounting in benchmarks. */
+int64_t dgdft_kernel_launches(void);
+
+/* ALB generation for all elements in one batched solve. */
+int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* params,
+                       dgdft_alb_result* result, dgdft_stream stream);
+
+/* DG blocks from a result of dgdft_alb_generate (eigvec, coef, alb used).
+ * blocks: DATA [M][n_stencil][L][L]; block (k, s) has rows = test ALBs of
+ * element k and columns = trial ALBs of neighbors[k][s] (Eq. DGHamiltonian).
+ * alpha is the penalty (Ha bohr).  The nonlocal coupling of a pair goes to the
+ * first slot naming it; faces along axes where E spans its domain are skipped. */
+int dgdft_dg_assemble(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* params,
+                      const dgdft_alb_result* result, double alpha, double* blocks, dgdft_stream stream);
+
+/* Band energy E_k = sum_j 2 f_j lambda_j (f Fermi-Dirac at kT, mu_k fixed by
+ * n_electrons[k], a host array) and its gradient: energy DATA [M],
+ * grad_v DATA [total points of all domains] (dE/dV at each grid point,
+ * including dV), grad_R DATA [n_atoms][3].  Uses eigval and eigvec. */
+int dgdft_alb_grad(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* params,
+                   const dgdft_alb_result* result, double kT, const double* n_electrons, double* energy,
+                   double* grad_v, double* grad_R, dgdft_stream stream);
+
+/* The hot operator: Y = H X for packed FP64 (precision DGDFT_FP64) or FP32
+ * (DGDFT_MIXED) blocks of params.n_blk vectors per element (device memory). */
+int dgdft_apply_hamiltonian(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* params,
+                            const void* X, void* Y, dgdft_stream stream);
+
+/* One Chebyshev filter pass Y = p_m(H) X of degree params.cheb_degree
+ * (Alg. CheFSI step 2: [b_low, b_up] mapped to [-1, 1], scaled at a0) with
+ * per-element bounds[k] = {a0, b_low, b_up} (host [M][3]), on packed blocks as
+ * in dgdft_apply_hamiltonian.  X is not modified. */
+int dgdft_chebyshev_filter(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* params,
+                           const double* bounds, const void* X, void* Y, dgdft_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGDFT_H */

@@ -1,0 +1,266 @@
+"""Python binding of libdgdft: argument marshalling only.
+
+Every step of the computation runs in the CUDA library; this module turns a
+``workloads.Problem`` / ``workloads.Params`` pair and torch device tensors
+into the C structures of include/dgdft.h and back.  It raises when the
+library is missing or a call fails; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _abi
+
+
+class DgdftError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_abi.STATUS_NAMES[code] if 0 <= code < len(_abi.STATUS_NAMES) else code}: {msg}")
+        self.code = code
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a), dtype=np.int32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a), dtype=np.float64)
+
+
+def _ptr(arr, ctype):
+    return arr.ctypes.data_as(C.POINTER(ctype))
+
+
+class Marshalled:
+    """Keeps the numpy buffers alive while the C structures point into them."""
+
+    def __init__(self, prob, params, *, precision, cheb_degree, tol, max_iter, tol_mixed=0.0,
+                 lanczos_steps=10, seed=None, flags=0, v_extra=None):
+        self.keep = []
+
+        def keep(a):
+            self.keep.append(a)
+            return a
+
+        p = _abi.Problem()
+        p.n_dom = int(prob.dom_n.shape[0])
+        p.dom_n = _ptr(keep(_i32(prob.dom_n)), C.c_int)
+        p.dom_h = _ptr(keep(_f64(prob.dom_h)), C.c_double)
+        p.dom_voff = _ptr(keep(np.ascontiguousarray(prob.dom_voff, dtype=np.int64)), C.c_int64)
+        p.v_extra = C.c_void_p(0 if v_extra is None else v_extra)
+        p.n_elem = int(prob.n_elem)
+        p.elem_dom = _ptr(keep(_i32(prob.elem_dom)), C.c_int)
+        p.elem_E0 = _ptr(keep(_i32(prob.elem_E0)), C.c_int)
+        p.elem_En = _ptr(keep(_i32(prob.elem_En)), C.c_int)
+        p.elem_Qn = _ptr(keep(_i32(prob.elem_Qn)), C.c_int)
+        p.neighbors = _ptr(keep(_i32(prob.neighbors)), C.c_int)
+        p.n_stencil = int(prob.n_stencil)
+        p.n_atoms = int(prob.n_atoms)
+        p.atom_dom = _ptr(keep(_i32(prob.atom_dom if prob.n_atoms else np.zeros(1))), C.c_int)
+        p.atom_pos = _ptr(keep(_f64(prob.atom_pos if prob.n_atoms else np.zeros(3))), C.c_double)
+        p.well_depth = _ptr(keep(_f64(prob.well_depth if prob.n_atoms else np.zeros(1))), C.c_double)
+        p.well_width = _ptr(keep(_f64(prob.well_width if prob.n_atoms else np.ones(1))), C.c_double)
+        p.n_proj_per_atom = int(prob.n_proj_per_atom)
+        pg = prob.proj_gamma if prob.proj_gamma.size else np.zeros(1)
+        p.proj_gamma = _ptr(keep(_f64(pg)), C.c_double)
+        p.proj_width = _ptr(keep(_f64(prob.proj_width if prob.n_atoms else np.ones(1))), C.c_double)
+        p.r_cut = float(prob.r_cut)
+        self.prob = p
+        q = _abi.AlbParams()
+        q.n_eig = _ptr(keep(_i32(params.n_eig)), C.c_int)
+        q.n_alb = _ptr(keep(_i32(params.n_alb)), C.c_int)
+        q.n_blk = _ptr(keep(_i32(params.n_blk)), C.c_int)
+        q.cheb_degree = int(cheb_degree)
+        q.tol = float(tol)
+        q.tol_mixed = float(tol_mixed)
+        q.max_iter = int(max_iter)
+        q.lanczos_steps = int(lanczos_steps)
+        q.precision = int(precision)
+        q.seed = int(params.seed if seed is None else seed)
+        q.flags = int(flags)
+        self.params = q
+
+
+class Context:
+    """A libdgdft context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = _abi.load()
+        h = C.c_void_p()
+        r = self.lib.dgdft_ctx_create(C.byref(h), int(device))
+        if r != 0:
+            raise DgdftError(r, "dgdft_ctx_create: " + self.lib.dgdft_last_error(None).decode())
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            self.lib.dgdft_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, r, allow=(0,)):
+        if r not in allow:
+            raise DgdftError(r, self.lib.dgdft_last_error(self.h).decode())
+        return r
+
+
+def query_sizes(m: Marshalled):
+    out = (C.c_int64 * 6)()
+    r = _abi.load().dgdft_alb_query_sizes(C.byref(m.prob), C.byref(m.params), out)
+    if r != 0:
+        raise DgdftError(r, "dgdft_alb_query_sizes")
+    return [int(v) for v in out]
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclass
+class ALBResult:
+    eigval: torch.Tensor
+    resid: torch.Tensor
+    sing: torch.Tensor
+    coef: torch.Tensor
+    alb: torch.Tensor
+    eigvec: torch.Tensor | None
+    iters: torch.Tensor
+    status: torch.Tensor
+    L: int
+    code: int
+    struct: object = None
+
+    def as_struct(self):
+        s = _abi.AlbResult()
+        for f in ("eigval", "resid", "sing", "coef", "alb", "iters", "status"):
+            setattr(s, f, C.c_void_p(getattr(self, f).data_ptr()))
+        s.eigvec = C.c_void_p(self.eigvec.data_ptr() if self.eigvec is not None else 0)
+        return s
+
+
+def v_extra_tensor(prob, device="cuda"):
+    return torch.as_tensor(np.ascontiguousarray(prob.v_extra, dtype=np.float64), device=device)
+
+
+def alb_generate(ctx: Context, prob, params, *, precision=_abi.FP64, cheb_degree=None, tol=None, max_iter=None,
+                 tol_mixed=0.0, keep_eigvec=True, v_extra=None, allow_not_converged=True, host_buffers=False):
+    """ALB generation for every element (dgdft_alb_generate).  Returns ALBResult of device tensors."""
+    dev = torch.device("cuda", ctx.device)
+    if v_extra is None and not host_buffers:
+        v_extra = v_extra_tensor(prob, dev)
+    m = Marshalled(prob, params, precision=precision,
+                   cheb_degree=params.cheb_degree if cheb_degree is None else cheb_degree,
+                   tol=params.tol if tol is None else tol,
+                   max_iter=params.max_iter if max_iter is None else max_iter, tol_mixed=tol_mixed,
+                   flags=_abi.HOST_BUFFERS if host_buffers else 0,
+                   v_extra=None if v_extra is None else v_extra.data_ptr())
+    L, n_alb_tot, n_vec_tot, ncoef, _, _ = query_sizes(m)
+    M = prob.n_elem
+    kw = dict(dtype=torch.float64, device="cpu" if host_buffers else dev)
+    if host_buffers:
+        kw["pin_memory"] = True
+    res = ALBResult(eigval=torch.empty(M, L, **kw), resid=torch.empty(M, L, **kw), sing=torch.empty(M, L, **kw),
+                    coef=torch.empty(M, L, L, **kw), alb=torch.empty(max(1, n_alb_tot), **kw),
+                    eigvec=(torch.empty(n_vec_tot, dtype=torch.float64, device=dev)
+                            if keep_eigvec and not host_buffers else None),
+                    iters=torch.empty(M, dtype=torch.int32, device=kw["device"], pin_memory=host_buffers),
+                    status=torch.empty(M, dtype=torch.int32, device=kw["device"], pin_memory=host_buffers),
+                    L=L, code=0)
+    s = res.as_struct()
+    allow = (0, _abi.NOT_CONVERGED) if allow_not_converged else (0,)
+    res.code = ctx.check(ctx.lib.dgdft_alb_generate(ctx.h, C.byref(m.prob), C.byref(m.params), C.byref(s),
+                                                    _stream()), allow)
+    res.struct = (m, s)
+    return res
+
+
+def apply_hamiltonian(ctx: Context, prob, params, X: torch.Tensor, precision=_abi.FP64):
+    """Y = H X for packed blocks of n_blk vectors per element (device tensors, float64 or float32)."""
+    m = Marshalled(prob, params, precision=precision, cheb_degree=max(2, params.cheb_degree), tol=params.tol,
+                   max_iter=params.max_iter, v_extra=v_extra_tensor(prob, X.device).data_ptr())
+    m.keep.append(v := v_extra_tensor(prob, X.device))
+    m.prob.v_extra = C.c_void_p(v.data_ptr())
+    Y = torch.empty_like(X)
+    ctx.check(ctx.lib.dgdft_apply_hamiltonian(ctx.h, C.byref(m.prob), C.byref(m.params), C.c_void_p(X.data_ptr()),
+                                              C.c_void_p(Y.data_ptr()), _stream()))
+    return Y
+
+
+def chebyshev_filter(ctx: Context, prob, params, X: torch.Tensor, bounds: np.ndarray, degree: int,
+                     precision=_abi.FP64):
+    """Y = p_m(H) X with per-element bounds (a0, b_low, b_up)."""
+    v = v_extra_tensor(prob, X.device)
+    m = Marshalled(prob, params, precision=precision, cheb_degree=degree, tol=params.tol,
+                   max_iter=params.max_iter, v_extra=v.data_ptr())
+    m.keep.append(v)
+    b = _f64(bounds)
+    Y = torch.empty_like(X)
+    ctx.check(ctx.lib.dgdft_chebyshev_filter(ctx.h, C.byref(m.prob), C.byref(m.params), _ptr(b, C.c_double),
+                                             C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr()), _stream()))
+    return Y
+
+
+def unpack_blocks(flat: torch.Tensor, counts, sizes):
+    """Split a packed buffer into per-element [count, size] views."""
+    out, o = [], 0
+    for c, s in zip(counts, sizes):
+        out.append(flat[o:o + c * s].view(c, s))
+        o += c * s
+    return out
+
+
+def dg_assemble(ctx: Context, prob, params, res: ALBResult, alpha: float):
+    """DG blocks [M, n_stencil, L, L] (dgdft_dg_assemble) from a result of alb_generate."""
+    m, s = res.struct
+    v = v_extra_tensor(prob, torch.device("cuda", ctx.device))
+    m.keep.append(v)
+    m.prob.v_extra = C.c_void_p(v.data_ptr())
+    M, L = prob.n_elem, res.L
+    blocks = torch.empty(M, int(prob.n_stencil), L, L, dtype=torch.float64, device=v.device)
+    ctx.check(ctx.lib.dgdft_dg_assemble(ctx.h, C.byref(m.prob), C.byref(m.params), C.byref(s), float(alpha),
+                                        C.c_void_p(blocks.data_ptr()), _stream()))
+    return blocks
+
+
+def alb_grad(ctx: Context, prob, params, res: ALBResult, kT: float, n_electrons):
+    """(energy [M], grad_v [points of all domains], grad_R [n_atoms, 3]) (dgdft_alb_grad)."""
+    m, s = res.struct
+    dev = torch.device("cuda", ctx.device)
+    nel = _f64(n_electrons)
+    energy = torch.empty(prob.n_elem, dtype=torch.float64, device=dev)
+    grad_v = torch.empty(int(prob.v_extra.size), dtype=torch.float64, device=dev)
+    grad_R = torch.empty(max(1, prob.n_atoms), 3, dtype=torch.float64, device=dev)
+    ctx.check(ctx.lib.dgdft_alb_grad(ctx.h, C.byref(m.prob), C.byref(m.params), C.byref(s), float(kT),
+                                     _ptr(nel, C.c_double), C.c_void_p(energy.data_ptr()),
+                                     C.c_void_p(grad_v.data_ptr()), C.c_void_p(grad_R.data_ptr()), _stream()))
+    return energy, grad_v, grad_R[:prob.n_atoms]
+
+
+def alb_views(prob, params, res: ALBResult):
+    """Per-element views: ALBs [n_alb, NE] and eigenvectors [n_eig, N] (if kept)."""
+    NE = np.prod(prob.elem_En, axis=1)
+    N = np.prod(prob.elem_Qn, axis=1)
+    A = unpack_blocks(res.alb, params.n_alb, NE)
+    X = unpack_blocks(res.eigvec, params.n_eig, N) if res.eigvec is not None else None
+    return A, X
+
+
+def dg_assemble_host(ctx: Context, prob, params, res: ALBResult, alpha: float):
+    """dg_assemble with host buffers (coef and blocks in pinned host memory, eigenvectors kept in the context)."""
+    m, s = res.struct
+    m.params.flags = _abi.HOST_BUFFERS
+    m.prob.v_extra = C.c_void_p(prob.v_extra.ctypes.data) if prob.v_extra is not None else C.c_void_p(0)
+    M, L = prob.n_elem, res.L
+    blocks = torch.empty(M, int(prob.n_stencil), L, L, dtype=torch.float64, pin_memory=True)
+    ctx.check(ctx.lib.dgdft_dg_assemble(ctx.h, C.byref(m.prob), C.byref(m.params), C.byref(s), float(alpha),
+                                        C.c_void_p(blocks.data_ptr()), _stream()))
+    return blocks
