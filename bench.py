@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--config", type=int, default=5)
-    ap.add_argument("--degree", type=int, default=40)
+    ap.add_argument("--degree", type=int, default=80)
     ap.add_argument("--max-iter", type=int, default=60)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--fp64-elements", type=int, default=64, help="elements in the FP64 GPU sample (0 = skip)")
@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--elements", type=int, default=0, help="use only the first n elements (smoke runs)")
+    ap.add_argument("--only-filter", action="store_true",
+                    help="time only the FP32 Chebyshev filter (degree --degree) on random blocks (profiling)")
     return ap.parse_args()
 
 
@@ -141,7 +143,7 @@ def oracle_sample(wl, cores, iters_sample, iters_full, degree):
 
 def run_reference(args, wl):
     cores = os.cpu_count() or 1
-    iters_full = 14  # FP64 CheFSI iterations of a 32x32x48 element at degree 40 (oracle, tol 1e-8)
+    iters_full = 12  # FP64 CheFSI iterations of a 32x32x48 element at degree 80 (tol 1e-8)
     vals = []
     desc = ""
     for i in range(args.warmup + args.steps):
@@ -327,6 +329,32 @@ def filter_roofline(ctx, api, _abi, wl, torch, stream, res):
             "step_ms": 1000 * t_step, "bytes_per_step": bytes_step, "peak_source": peak[1]}
 
 
+def run_filter_only(args, wl):
+    import torch
+    from paper_2003_00407_gb300 import api, _abi
+    ctx = api.Context(0)
+    p, q = wl.problem, wl.params
+    N = np.prod(p.elem_Qn, axis=1).astype(np.int64)
+    nb = q.n_blk.astype(np.int64)
+    X = torch.randn(int(np.sum(nb * N)), dtype=torch.float32, device="cuda")
+    bounds = np.tile([-0.5, 1.0, 95.0], (p.n_elem, 1))
+    stream = torch.cuda.current_stream()
+    ts = []
+    for i in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        api.chebyshev_filter(ctx, p, q, X, bounds, args.degree, precision=_abi.MIXED)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ts.append(a.elapsed_time(b))
+    ms = statistics.median(ts)
+    by = float(np.sum(12 * N * nb + 4 * N)) * args.degree
+    print(json.dumps({"mode": "filter-only", "elements": int(p.n_elem), "degree": args.degree, "ms": ms,
+                      "GBps_algorithmic": by / ms / 1e6}), flush=True)
+    ctx.close()
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -350,6 +378,9 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             run_reference(args, wl)
+        return
+    if args.only_filter:
+        run_filter_only(args, wl)
         return
     if world > 1:
         import torch

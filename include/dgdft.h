@@ -124,6 +124,9 @@ typedef struct {
   double* eigvec;   /* packed [n_eig][N] per element: eigenvectors on Q_k, dV-orthonormal */
   int* iters;       /* [M] filter passes (both stages in mixed mode) */
   int* status;      /* [M] per-element status: 0 ok, or a dgdft_status */
+  double* history;  /* HOST, optional (NULL): [max_iter + 2] largest residual over the still-active
+                       elements after the start-up Rayleigh-Ritz (entry 0) and after each filter
+                       pass of the first stage; unused entries are set to -1 */
 } dgdft_alb_result;
 
 /* Sizes (in scalars) of the result arrays for a problem:

@@ -34,7 +34,8 @@ class AlbParams(C.Structure):
 
 class AlbResult(C.Structure):
     _fields_ = [("eigval", C.c_void_p), ("resid", C.c_void_p), ("sing", C.c_void_p), ("coef", C.c_void_p),
-                ("alb", C.c_void_p), ("eigvec", C.c_void_p), ("iters", C.c_void_p), ("status", C.c_void_p)]
+                ("alb", C.c_void_p), ("eigvec", C.c_void_p), ("iters", C.c_void_p), ("status", C.c_void_p),
+                ("history", C.c_void_p)]
 
 
 FUNCTIONS = {

@@ -138,12 +138,14 @@ class ALBResult:
     L: int
     code: int
     struct: object = None
+    history: np.ndarray = None
 
     def as_struct(self):
         s = _abi.AlbResult()
         for f in ("eigval", "resid", "sing", "coef", "alb", "iters", "status"):
             setattr(s, f, C.c_void_p(getattr(self, f).data_ptr()))
         s.eigvec = C.c_void_p(self.eigvec.data_ptr() if self.eigvec is not None else 0)
+        s.history = C.c_void_p(self.history.ctypes.data if self.history is not None else 0)
         return s
 
 
@@ -175,6 +177,7 @@ def alb_generate(ctx: Context, prob, params, *, precision=_abi.FP64, cheb_degree
                     iters=torch.empty(M, dtype=torch.int32, device=kw["device"], pin_memory=host_buffers),
                     status=torch.empty(M, dtype=torch.int32, device=kw["device"], pin_memory=host_buffers),
                     L=L, code=0)
+    res.history = np.full(int(m.params.max_iter) + 2, -1.0)
     s = res.as_struct()
     allow = (0, _abi.NOT_CONVERGED) if allow_not_converged else (0,)
     res.code = ctx.check(ctx.lib.dgdft_alb_generate(ctx.h, C.byref(m.prob), C.byref(m.params), C.byref(s),

@@ -18,7 +18,7 @@ struct dgdft_ctx {
   std::string err;
   std::map<std::string, std::pair<void*, size_t>> bufs;
   bool tw_ready = false;
-  int* h_active = nullptr;  // pinned readback of the active-element count
+  int* h_active = nullptr;  // pinned readback: active-element count and the max residual
 };
 
 namespace dgdft {
@@ -68,7 +68,8 @@ int init_twiddles(dgdft_ctx* ctx) {
       t64[twiddle_offset(n) + m] = make_double2(std::cos(a), std::sin(a));
       t32[twiddle_offset(n) + m] = make_float2(float(std::cos(a)), float(std::sin(a)));
     }
-  if (upload_twiddles(t64.data(), t32.data())) return fail(ctx, DGDFT_CUDA_ERROR, "twiddle upload failed");
+  if (upload_twiddles(t64.data(), t32.data()) || upload_fused_twiddles(t32.data()))
+    return fail(ctx, DGDFT_CUDA_ERROR, "twiddle upload failed");
   if (set_hx_smem_limits() || set_linalg_smem_limits()) {
     cudaGetLastError();
     return fail(ctx, DGDFT_CUDA_ERROR, "cudaFuncSetAttribute(max dynamic shared memory) failed");
@@ -95,6 +96,10 @@ int upload_plan(dgdft_ctx* ctx, Plan& P, cudaStream_t st) {
   if ((r = up("p_desc", P.desc.data(), P.desc.size() * sizeof(ElemDesc), (void**)&P.d_desc))) return r;
   if ((r = up("p_boxes", P.boxes.data(), P.boxes.size() * sizeof(AtomBox), (void**)&P.d_boxes))) return r;
   if ((r = up("p_dtab", P.dtab.data(), P.dtab.size() * sizeof(double), (void**)&P.d_dtab))) return r;
+  if ((r = up("p_dtab32", P.dtab32.data(), P.dtab32.size() * sizeof(float), (void**)&P.d_dtab32))) return r;
+  if ((r = up("p_fatoms", P.fatoms.data(), std::max<size_t>(1, P.fatoms.size()) * sizeof(FusedAtomRec),
+              (void**)&P.d_fatoms)))
+    return r;
   const char* names[kOffKinds] = {"p_ox", "p_oe", "p_oa", "p_ov", "p_os", "p_ofe", "p_ove"};
   for (int i = 0; i < kOffKinds; i++)
     if ((r = up(names[i], P.off[i].data(), P.off[i].size() * sizeof(long long), (void**)&P.d_off[i]))) return r;
@@ -106,6 +111,13 @@ int upload_plan(dgdft_ctx* ctx, Plan& P, cudaStream_t st) {
   g_max_points = P.max_points;
   g_max_nblk = P.max_nblk;
   g_max_nalb = P.max_nalb;
+  // radial factor tables of the fused FP32 kernel
+  P.d_gtab = (float*)ws(ctx, "p_gtab", std::max<long long>(1, P.tot_gtab) * sizeof(float));
+  if (!P.d_gtab) return fail(ctx, DGDFT_OUT_OF_MEMORY, "workspace allocation failed: p_gtab");
+  if (P.n_proj_per_atom > 0) {
+    BatchArgs b{P.d_desc, nullptr, P.M};
+    launch_build_gtab(b, P.d_fatoms, P.d_dtab32, float(P.r_cut), P.max_pa, P.d_gtab, st);
+  }
   return DGDFT_OK;
 }
 
@@ -121,6 +133,9 @@ HxArgs hx_args(const Plan& P, const int* flags, int kind, int nvec_mode) {
   a.nvec_mode = nvec_mode;
   a.n_proj_per_atom = P.n_proj_per_atom;
   a.r_cut = P.r_cut;
+  a.fatoms = P.d_fatoms;
+  a.dtab32 = P.d_dtab32;
+  a.gtab = P.d_gtab;
   return a;
 }
 
@@ -137,7 +152,7 @@ template <typename T> struct Stage {
 };
 
 struct Common {
-  double *V64, *bounds, *cheb, *G1, *G2, *W, *theta, *resid2, *resid, *P, *prevres, *alphas, *betas, *ldot;
+  double *V64, *bounds, *cheb, *G1, *G2, *W, *theta, *resid2, *resid, *P, *prevres, *alphas, *betas, *ldot, *lmin;
   float* V32;
   int *flags, *iters, *stall, *active, *hitcap;
 };
@@ -198,10 +213,11 @@ int get_common(dgdft_ctx* ctx, const Plan& P, int degree, int lsteps, Common& c)
   WS(c.alphas, "alphas", M * lsteps * sizeof(double));
   WS(c.betas, "betas", M * lsteps * sizeof(double));
   WS(c.ldot, "ldot", M * sizeof(double));
+  WS(c.lmin, "lmin", M * sizeof(double));
   WS(c.flags, "flags", M * sizeof(int));
   WS(c.iters, "iters", M * sizeof(int));
   WS(c.stall, "stall", M * sizeof(int));
-  WS(c.active, "active", sizeof(int));
+  WS(c.active, "active", 4 * sizeof(int));   // [0] active count, [2..3] max residual (double bits)
   WS(c.hitcap, "hitcap", M * sizeof(int));
   return DGDFT_OK;
 }
@@ -249,7 +265,7 @@ void lanczos(Plan& P, const Common& c, Stage<T>& s, int steps, cudaStream_t st) 
   }
   cudaMemsetAsync(c.ldot, 0, P.M * sizeof(double), st);
   launch_dot<T>(b, s.Lf, s.Lf, ov, c.ldot, 1, st);
-  launch_lanczos_bound(b, c.alphas, c.betas, steps, c.ldot, c.bounds, st);
+  launch_lanczos_bound(b, c.alphas, c.betas, steps, c.ldot, c.bounds, c.lmin, st);
 }
 
 // Rayleigh-Ritz of the orthonormalised block Y: X -> B[0], HX -> HY, theta, residuals
@@ -282,7 +298,9 @@ void cholqr(Plan& P, const Common& c, T* Y, double rel_shift, cudaStream_t st) {
 // promoted); on exit B[0] holds the Ritz vectors of every element.
 template <typename T>
 int chefsi_stage(dgdft_ctx* ctx, Plan& P, const Common& c, Stage<T>& s, const dgdft_alb_params* prm, int degree,
-                 int lsteps, bool mixed, cudaStream_t st) {
+                 int lsteps, bool mixed, cudaStream_t st, double* history) {
+  if (history)
+    for (int i = 0; i < prm->max_iter + 2; i++) history[i] = -1.0;
   BatchArgs b{P.d_desc, c.flags, P.M};
   const double rel_shift = sizeof(T) == 4 ? 1e-6 : 1e-13;
   lanczos<T>(P, c, s, lsteps, st);
@@ -290,13 +308,19 @@ int chefsi_stage(dgdft_ctx* ctx, Plan& P, const Common& c, Stage<T>& s, const dg
   cholqr<T>(P, c, s.B[0], rel_shift, st);
   rayleigh_ritz<T>(P, c, s, s.B[0], st);
   const double tol_mixed = prm->tol_mixed > 0 ? prm->tol_mixed : 1e-6;
-  cudaMemsetAsync(c.active, 0, sizeof(int), st);
+  cudaMemsetAsync(c.active, 0, 4 * sizeof(int), st);
   launch_update_convergence(b, c.resid2, P.L, c.resid, c.theta, c.bounds, prm->tol, tol_mixed, mixed ? 1 : 0,
                             c.prevres, c.stall, c.flags, c.active, c.iters, st);
+  launch_first_a0(b, c.lmin, c.bounds, st);
   // the start Rayleigh-Ritz is not a filter pass
   for (int it = 0; it <= prm->max_iter; it++) {
-    CUDA_OK(cudaMemcpyAsync(ctx->h_active, c.active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_OK(cudaMemcpyAsync(ctx->h_active, c.active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_OK(cudaStreamSynchronize(st));
+    if (history) {
+      double mx;
+      std::memcpy(&mx, ctx->h_active + 2, sizeof(double));
+      history[it] = mx;
+    }
     if (*ctx->h_active == 0) break;
     if (it == prm->max_iter) {
       // elements still active hit the cap
@@ -321,7 +345,7 @@ int chefsi_stage(dgdft_ctx* ctx, Plan& P, const Common& c, Stage<T>& s, const dg
     }
     cholqr<T>(P, c, cur, rel_shift, st);
     rayleigh_ritz<T>(P, c, s, cur, st);
-    cudaMemsetAsync(c.active, 0, sizeof(int), st);
+    cudaMemsetAsync(c.active, 0, 4 * sizeof(int), st);
     launch_update_convergence(b, c.resid2, P.L, c.resid, c.theta, c.bounds, prm->tol, tol_mixed, mixed ? 1 : 0,
                               c.prevres, c.stall, c.flags, c.active, c.iters, st);
   }
@@ -362,7 +386,7 @@ int dgdft_ctx_create(dgdft_ctx** out, int device) {
   if (cudaSetDevice(device) != cudaSuccess) return fail(nullptr, DGDFT_CUDA_ERROR, "cudaSetDevice failed");
   dgdft_ctx* c = new dgdft_ctx();
   c->device = device;
-  if (cudaMallocHost(&c->h_active, sizeof(int)) != cudaSuccess) {
+  if (cudaMallocHost(&c->h_active, 4 * sizeof(int)) != cudaSuccess) {
     delete c;
     return fail(nullptr, DGDFT_CUDA_ERROR, "cudaMallocHost failed");
   }
@@ -415,7 +439,7 @@ int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_al
     vx = d;
   }
   CUDA_OK(cudaMemsetAsync(c.flags, 0, M * sizeof(int), st));
-  CUDA_OK(cudaMemsetAsync(c.iters, 0, M * sizeof(int), st));
+  CUDA_OK(cudaMemsetAsync(c.iters, 0xFF, M * sizeof(int), st));   // -1: the start-up Rayleigh-Ritz is not a pass
   CUDA_OK(cudaMemsetAsync(c.stall, 0, M * sizeof(int), st));
   CUDA_OK(cudaMemsetAsync(c.hitcap, 0, M * sizeof(int), st));
   CUDA_OK(cudaMemsetAsync(c.bounds, 0, M * 3 * sizeof(double), st));
@@ -435,7 +459,7 @@ int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_al
     const int u32[4] = {0, 1, 2, 3};
     if ((r = get_stage<float>(ctx, P, s32, 6, u32))) return r;
     launch_random_init<float>(ball, s32.B[0], P.d_off[OFF_X], prm->seed, st);
-    if ((r = chefsi_stage<float>(ctx, P, c, s32, prm, degree, lsteps, true, st))) return r;
+    if ((r = chefsi_stage<float>(ctx, P, c, s32, prm, degree, lsteps, true, st, res->history))) return r;
     // final FP64 Rayleigh-Ritz sweep on the FP32 Ritz vectors: X64 in place, HX64 over B1/B2 of the FP32 stage
     const int u64[4] = {4, 4, 4, 1};
     if ((r = get_stage<double>(ctx, P, s64, 6, u64))) return r;
@@ -452,7 +476,7 @@ int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_al
     const int u64[4] = {0, 2, 4, 6};
     if ((r = get_stage<double>(ctx, P, s64, 8, u64))) return r;
     launch_random_init<double>(ball, s64.B[0], P.d_off[OFF_X], prm->seed, st);
-    if ((r = chefsi_stage<double>(ctx, P, c, s64, prm, degree, lsteps, false, st))) return r;
+    if ((r = chefsi_stage<double>(ctx, P, c, s64, prm, degree, lsteps, false, st, res->history))) return r;
     X64 = s64.B[0];
   }
   CUDA_OK(cudaGetLastError());

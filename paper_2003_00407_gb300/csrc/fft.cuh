@@ -123,7 +123,7 @@ __device__ __forceinline__ void line_pass1(const cplx<T>* __restrict__ src, int 
   dft<R, DIR>(a);
 #pragma unroll
   for (int k1 = 0; k1 < R; k1++) {
-    cplx<T> w = twiddle<T>(n, (t * k1) % n);
+    cplx<T> w = twiddle<T>(n, t * k1);  // t*k1 <= (n2-1)(n1-1) < n
     if (DIR > 0) w.im = -w.im;
     tl[k1 * n2 + t] = cmul(a[k1], w);
   }

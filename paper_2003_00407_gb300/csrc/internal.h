@@ -36,6 +36,19 @@ struct ElemDesc {
   long long troff;  // face traces [6 faces][2 kinds][n_alb][fmax] (DG)
   int fmax;         // largest face (points) of E
   int face_mask;    // bit (axis*2 + side) set when that face carries DG terms
+  int tab_off, tab_len;  // the element's Q-box displacement tables in dtab (contiguous)
+  long long gtab_off;    // radial factor table g of the Q boxes: [pa_count][16 z][16 y][16 x] floats
+  float kscale[3];  // 1/2 (2 pi / (n_a h_a))^2 / N: kinetic multiplier per m_a^2
+};
+
+// FP32 record of an atom box meeting Q, for the fused Chebyshev kernel
+// (parallel to the Q boxes; toff is relative to the element's tab_off).
+struct FusedAtomRec {
+  int s[3], l[3];
+  int toff, pad;
+  float inv2s2;     // 1 / (2 sigma^2) of the projector radial Gaussian
+  float c[4];       // gamma_l N_l^2 dV for s, px, py, pz (0 when absent)
+  float pad2;
 };
 
 // An atom whose support box meets a region (Q or E) of one element.  The box

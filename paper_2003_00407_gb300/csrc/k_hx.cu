@@ -15,6 +15,8 @@
 
 namespace dgdft {
 
+constexpr int kMaxPlaneAtoms = 160;
+
 int upload_twiddles(const double2* t64, const float2* t32) {
   if (cudaMemcpyToSymbol(g_tw64, t64, sizeof(double2) * kTwiddleCount) != cudaSuccess) return 1;
   if (cudaMemcpyToSymbol(g_tw32, t32, sizeof(float2) * kTwiddleCount) != cudaSuccess) return 1;
@@ -32,7 +34,9 @@ __host__ int plane_smem_bytes(int qx, int qy, int elem_bytes) {
   return r + c1 + c2 + tmp * c + sp + 16 * 4 * 8 + 1024;  // + projector partials, atom list
 }
 
-__host__ int zline_smem_bytes(int qz, int chunk, int elem_bytes) { return 2 * qz * chunk * 2 * elem_bytes; }
+__host__ int zline_smem_bytes(int qz, int chunk, int elem_bytes) {
+  return 2 * qz * chunk * 2 * elem_bytes + 3 * kMaxLine * elem_bytes;
+}
 
 // Gaussian-radial projector/well factor g = exp(-d^2 / 2 s^2) (1 - d^2/rc^2)^3 inside rc, else 0
 template <typename T> __device__ __forceinline__ T radial_g(T d2, T inv2s2, T inv_rc2) {
@@ -149,31 +153,36 @@ __global__ void __launch_bounds__(256) k_zline(HxArgs a, cplx<T>* __restrict__ S
   }
   __syncthreads();
   fft_lines<-1, T>(buf, 1, chunk, buf, 1, chunk, tmp, chunk, d.fz[0], d.fz[1]);
+  // multiplier tables per axis: kinetic 1/2 G_a^2 / N, or G_a / N for a derivative (Nyquist dropped)
+  T* tab = reinterpret_cast<T*>(tmp + qz * chunk);   // [3][kMaxLine]: x, y, z
   const double invN = 1.0 / double(d.N);
   const double twopi = 6.283185307179586476925;
+  for (int i = threadIdx.x; i < 3 * kMaxLine; i += blockDim.x) {
+    const int ax = i / kMaxLine, kk = i - ax * kMaxLine;
+    const int n = ax == 0 ? qx : (ax == 1 ? qy : qz);
+    T v = T(0);
+    if (kk < n) {
+      const int m = kk <= n / 2 ? kk : kk - n;
+      const double g = twopi * m / (n * d.h[ax]);
+      if (mode == MULT_KINETIC) v = T(0.5 * g * g * invN);
+      else if (mode == MULT_DX + ax) v = (n % 2 == 0 && kk == n / 2) ? T(0) : T(g * invN);
+    }
+    tab[i] = v;
+  }
+  __syncthreads();
+  const T sc = T(invN);
   for (int i = threadIdx.x; i < qz * chunk; i += blockDim.x) {
     const int kz = i / chunk, c = i - kz * chunk;
     const int col = c0 + c;
     if (col >= ncol) continue;
     const int ky = col / hx, kx = col - ky * hx;
-    const int my = ky <= qy / 2 ? ky : ky - qy;
-    const int mz = kz <= qz / 2 ? kz : kz - qz;
-    const double gx = twopi * kx / (qx * d.h[0]);
-    const double gy = twopi * my / (qy * d.h[1]);
-    const double gz = twopi * mz / (qz * d.h[2]);
     cplx<T> s = buf[i];
     if (mode == MULT_KINETIC) {
-      const T f = T(0.5 * (gx * gx + gy * gy + gz * gz) * invN);
-      s = cscale(s, f);
+      s = cscale(s, tab[kx] + tab[kMaxLine + ky] + tab[2 * kMaxLine + kz]);
     } else if (mode == MULT_SCALE) {
-      s = cscale(s, T(invN));
+      s = cscale(s, sc);
     } else {
-      // i G_axis / N with the Nyquist coefficient dropped
-      double g = 0.0;
-      if (mode == MULT_DX) g = (qx % 2 == 0 && kx == qx / 2) ? 0.0 : gx;
-      if (mode == MULT_DY) g = (qy % 2 == 0 && ky == qy / 2) ? 0.0 : gy;
-      if (mode == MULT_DZ) g = (qz % 2 == 0 && kz == qz / 2) ? 0.0 : gz;
-      const T f = T(g * invN);
+      const T f = mode == MULT_DX ? tab[kx] : (mode == MULT_DY ? tab[kMaxLine + ky] : tab[2 * kMaxLine + kz]);
       s = cplx<T>{-s.im * f, s.re * f};
     }
     buf[i] = s;
@@ -207,18 +216,27 @@ __global__ void __launch_bounds__(256) k_plane_inverse(HxArgs a, const cplx<T>* 
   cplx<T>* Sp = tmp + tmpn;
   int* alist = reinterpret_cast<int*>(Sp + qy * hx);
   __shared__ int na_list;
-
+  __shared__ T acoef[kMaxPlaneAtoms][6];  // gamma_l N_l <b_l, x> for s, px, py, pz; 1/(2 sigma^2)
   const cplx<T>* sp = S + a.so[k] + (long long)v * d.qn[2] * qy * hx + (long long)z * qy * hx;
   for (int i = threadIdx.x; i < qy * hx; i += blockDim.x) Sp[i] = sp[i];
   if (threadIdx.x == 0) {
     // atom boxes that meet this plane (for the nonlocal term)
     int n = 0;
     if (out_mode != OUT_RAW && P != nullptr && a.n_proj_per_atom > 0) {
-      for (int ai = 0; ai < d.pa_count && n < 256; ai++) {
+      const double* pv0 = P + d.poff + (long long)v * d.n_proj;
+      for (int ai = 0; ai < d.pa_count && n < kMaxPlaneAtoms; ai++) {
         const AtomBox& b = a.boxes[d.pa_begin + ai];
         int iz = z - b.s[2];
         if (iz < 0) iz += d.qn[2];
-        if (iz < b.l[2]) alist[n++] = ai;
+        if (iz < b.l[2]) {
+          alist[n] = ai;
+          acoef[n][0] = T(b.gamma[0] * b.ns * pv0[b.col]);
+          for (int l = 1; l < 4; l++)
+            acoef[n][l] = a.n_proj_per_atom == 4 ? T(b.gamma[l] * b.np * pv0[b.col + l]) : T(0);
+          acoef[n][4] = T(0.5 / (b.pwidth * b.pwidth));
+          acoef[n][5] = T(b.l[0] + b.l[1] + iz);   // dtab index of this plane's z displacement (relative)
+          n++;
+        }
       }
     }
     na_list = n;
@@ -258,7 +276,6 @@ __global__ void __launch_bounds__(256) k_plane_inverse(HxArgs a, const cplx<T>* 
     beta = cheb[k * cheb_stride + 2];
   }
   const T* vq = V + d.voff + (long long)z * qy * qx;
-  const double* pv = P ? P + d.poff + (long long)v * d.n_proj : nullptr;
   const T inv_rc2 = T(1.0 / (a.r_cut * a.r_cut));
   const int nal = na_list;
   for (int i = threadIdx.x; i < qy * qx; i += blockDim.x) {
@@ -273,17 +290,12 @@ __global__ void __launch_bounds__(256) k_plane_inverse(HxArgs a, const cplx<T>* 
       if (iy >= b.l[1]) continue;
       int ix = x - b.s[0]; if (ix < 0) ix += qx;
       if (ix >= b.l[0]) continue;
-      int iz = z - b.s[2]; if (iz < 0) iz += d.qn[2];
       const double* tx0 = a.dtab + b.toff;
-      const T dx = T(tx0[ix]), dy = T(tx0[b.l[0] + iy]), dz = T(tx0[b.l[0] + b.l[1] + iz]);
-      const T g = radial_g(dx * dx + dy * dy + dz * dz, T(0.5 / (b.pwidth * b.pwidth)), inv_rc2);
+      const T* ac = acoef[li];
+      const T dx = T(tx0[ix]), dy = T(tx0[b.l[0] + iy]), dz = T(tx0[int(ac[5])]);
+      const T g = radial_g(dx * dx + dy * dy + dz * dz, ac[4], inv_rc2);
       if (g == T(0)) continue;
-      T s = T(b.gamma[0] * b.ns * pv[b.col]);
-      if (a.n_proj_per_atom == 4) {
-        s += T(b.gamma[1] * b.np * pv[b.col + 1]) * dx + T(b.gamma[2] * b.np * pv[b.col + 2]) * dy +
-             T(b.gamma[3] * b.np * pv[b.col + 3]) * dz;
-      }
-      hxv += g * s;
+      hxv += g * (ac[0] + ac[1] * dx + ac[2] * dy + ac[3] * dz);
     }
     T out;
     if (out_mode == OUT_CHEB) {
@@ -303,6 +315,11 @@ void launch_hx(const HxPlan& pl, const HxArgs& args, const T* X, T* Y, const T* 
   for (const ShapeGroup& g : pl.groups) {
     HxArgs a = args;
     a.elems = g.d_elems;
+    if constexpr (sizeof(T) == 4) {
+      if (mult_mode == MULT_KINETIC && out_mode != OUT_RAW && g.fused_ok &&
+          launch_fused_group(g, a, X, Y, Yprev, V, cheb, cheb_stride, out_mode, st))
+        continue;
+    }
     const int eb = sizeof(T);
     const int smA = plane_smem_bytes(g.qn[0], g.qn[1], eb);
     const int chunk = g.zchunk;

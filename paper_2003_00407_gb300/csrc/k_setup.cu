@@ -165,10 +165,11 @@ __global__ void k_alb_sign(BatchArgs b, double* A, const long long* ao, double* 
   if (j >= d.n_alb) return;
   double* Aj = A + ao[k] + (long long)j * d.NE;
   double best = -1.0;
-  int bi = 0x7fffffff;
+  int bi = 0;
+  bool first = true;
   for (int e = threadIdx.x; e < d.NE; e += blockDim.x) {
-    const double a = fabs(Aj[e]);
-    if (a > best || (a == best && e < bi)) { best = a; bi = e; }
+    const double a = fabs(Aj[e]);   // NaN entries never win (comparisons are false)
+    if (first || a > best || (a == best && e < bi)) { best = isnan(a) ? -1.0 : a; bi = e; first = false; }
   }
   __shared__ double sb[256];
   __shared__ int si[256];
@@ -186,7 +187,8 @@ __global__ void k_alb_sign(BatchArgs b, double* A, const long long* ao, double* 
     }
     __syncthreads();
   }
-  const bool flip = Aj[si[0]] < 0.0;
+  const int ibest = (si[0] >= 0 && si[0] < d.NE) ? si[0] : 0;
+  const bool flip = Aj[ibest] < 0.0;
   __syncthreads();
   if (!flip) return;
   for (int e = threadIdx.x; e < d.NE; e += blockDim.x) Aj[e] = -Aj[e];
@@ -210,6 +212,7 @@ __global__ void k_update_convergence(BatchArgs b, const double* resid2, int ldr,
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.M) return;
   if (!(flags[k] & EF_ACTIVE)) return;
+  unsigned long long* hist_max = reinterpret_cast<unsigned long long*>(active_count + 2);
   const ElemDesc& d = b.desc[k];
   double mx = 0.0;
   for (int j = 0; j < d.n_blk; j++) {
@@ -223,11 +226,15 @@ __global__ void k_update_convergence(BatchArgs b, const double* resid2, int ldr,
   bool done = mx <= tol || !isfinite(mx);
   if (!isfinite(mx)) atomicOr(&flags[k], EF_BAD);
   if (mixed) {
+    // FP32 stage: stop at tol_mixed, or after two iterations that reduce the residual by less
+    // than 20% (the FP32 floor; the subspace keeps improving while the residual, dominated by
+    // high-energy rounding noise, stagnates, so the second stagnating pass is kept)
     if (mx <= tol_mixed) done = true;
     if (mx > 0.8 * prev_res[k]) stall[k] += 1; else stall[k] = 0;
     if (stall[k] >= 2) done = true;
   }
   prev_res[k] = mx;
+  if (isfinite(mx)) atomicMax(hist_max, (unsigned long long)__double_as_longlong(mx));
   if (done) atomicAnd(&flags[k], ~EF_ACTIVE);
   else atomicAdd(active_count, 1);
 }
@@ -337,7 +344,7 @@ void launch_scale_vec_old(const BatchArgs& b, T* v, const T* f, T* vold, const l
 
 // largest eigenvalue of the Lanczos tridiagonal (bisection on Sturm counts) + |f|
 __global__ void k_lanczos_bound(BatchArgs b, const double* alphas, const double* betas, int steps,
-                                const double* fnorm2, double* bounds) {
+                                const double* fnorm2, double* bounds, double* lanczos_min) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.M) return;
   const double* al = alphas + (long long)k * steps;
@@ -348,9 +355,8 @@ __global__ void k_lanczos_bound(BatchArgs b, const double* alphas, const double*
     lo = fmin(lo, al[j] - r);
     hi = fmax(hi, al[j] + r);
   }
-  // count of eigenvalues < x via the LDL^T pivots
-  for (int it = 0; it < 200; it++) {
-    const double x = 0.5 * (lo + hi);
+  // count of eigenvalues < x via the LDL^T pivots (Sturm sequence)
+  auto count_below = [&](double x) {
     int cnt = 0;
     double q = 1.0;
     for (int j = 0; j < steps; j++) {
@@ -359,13 +365,35 @@ __global__ void k_lanczos_bound(BatchArgs b, const double* alphas, const double*
       if (q == 0.0) q = -1e-300;
       if (q < 0.0) cnt++;
     }
-    if (cnt >= steps) hi = x; else lo = x;
+    return cnt;
+  };
+  const double lo0 = lo, hi0 = hi;
+  for (int it = 0; it < 200; it++) {   // largest Ritz value
+    const double x = 0.5 * (lo + hi);
+    if (count_below(x) >= steps) hi = x; else lo = x;
   }
   bounds[3 * k + 2] = hi + sqrt(fmax(fnorm2[k], 0.0));
+  lo = lo0; hi = hi0;
+  for (int it = 0; it < 200; it++) {   // smallest Ritz value
+    const double x = 0.5 * (lo + hi);
+    if (count_below(x) >= 1) hi = x; else lo = x;
+  }
+  lanczos_min[k] = lo;
 }
 void launch_lanczos_bound(const BatchArgs& b, const double* alphas, const double* betas, int steps,
-                          const double* fnorm2, double* bounds, cudaStream_t st) {
-  count_launch(); k_lanczos_bound<<<(b.M + 127) / 128, 128, 0, st>>>(b, alphas, betas, steps, fnorm2, bounds);
+                          const double* fnorm2, double* bounds, double* lanczos_min, cudaStream_t st) {
+  count_launch(); k_lanczos_bound<<<(b.M + 127) / 128, 128, 0, st>>>(b, alphas, betas, steps, fnorm2, bounds,
+                                                                     lanczos_min);
+}
+
+// first filter pass: scale at min(start-up Ritz minimum, Lanczos minimum) so that components below the
+// start block's Ritz values cannot be amplified beyond the FP32 range
+__global__ void k_first_a0(BatchArgs b, const double* lanczos_min, double* bounds) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < b.M) bounds[3 * k] = fmin(bounds[3 * k], lanczos_min[k]);
+}
+void launch_first_a0(const BatchArgs& b, const double* lanczos_min, double* bounds, cudaStream_t st) {
+  count_launch(); k_first_a0<<<(b.M + 127) / 128, 128, 0, st>>>(b, lanczos_min, bounds);
 }
 
 template void launch_random_init<float>(const BatchArgs&, float*, const long long*, unsigned long long, cudaStream_t);

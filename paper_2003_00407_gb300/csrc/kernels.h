@@ -10,6 +10,8 @@ constexpr int kMaxLine = 64;
 constexpr int kTwiddleCount = kMaxLine * (kMaxLine + 1) / 2;
 __host__ __device__ constexpr int twiddle_offset(int n) { return n * (n - 1) / 2; }
 int upload_twiddles(const double2* t64, const float2* t32);
+int upload_fused_twiddles(const float2* t32);
+constexpr int kFusedAtomLimit = 96, kFusedTabLimit = 2048;
 
 // Kernel launches issued by this library since it was loaded (reported by dgdft_kernel_launches).
 extern long long g_launches;
@@ -30,6 +32,9 @@ struct HxArgs {
   int nvec_mode;
   int n_proj_per_atom;
   double r_cut;
+  const FusedAtomRec* fatoms;  // FP32 atom records (fused kernel)
+  const float* dtab32;
+  const float* gtab;           // radial factor tables (fused kernel)
 };
 
 struct ShapeGroup {
@@ -38,6 +43,7 @@ struct ShapeGroup {
   int max_nvec;          // set by the launcher for the current mode
   int max_nblk, max_neig, max_nalb;
   int zchunk;
+  bool fused_ok;         // every element's atom boxes fit the fused kernel's tables
   int* d_elems;          // device list of element ids
   std::vector<int> elems;
 };
@@ -45,6 +51,10 @@ struct ShapeGroup {
 struct HxPlan {
   std::vector<ShapeGroup> groups;
 };
+
+// fused FP32 Chebyshev step (k_fused.cu): returns 1 when it handled the group
+int launch_fused_group(const ShapeGroup& g, const HxArgs& h, const float* X, float* Y, const float* Yprev,
+                       const float* V, const double* cheb, int cheb_stride, int out_mode, cudaStream_t st);
 
 int plane_smem_bytes(int qx, int qy, int elem_bytes);
 // Raise a kernel's dynamic shared-memory limit to the device opt-in maximum
@@ -84,6 +94,9 @@ template <typename TI>
 void launch_gram(const BatchArgs& b, const TI* A, const long long* ao, int na_mode, const TI* B, const long long* bo,
                  int nb_mode, int npts_mode, const double* weight, const long long* wo, double* G, int ldg,
                  cudaStream_t st, double scale = 1.0);
+// radial factor tables g of every element's Q boxes (k_fused.cu)
+void launch_build_gtab(const BatchArgs& b, const FusedAtomRec* fatoms, const float* dtab32, float r_cut, int max_pa,
+                       float* gtab, cudaStream_t st);
 // Z_k[j][p] = sum_i W_k[i][j] X_k[i][p] (in place allowed), optional second block and residuals
 template <typename TX, typename TZ>
 void launch_rotate(const BatchArgs& b, const TX* X, const long long* xo, TZ* Z, const long long* zo, int nin_mode,
@@ -131,7 +144,8 @@ void launch_scale_vec_old(const BatchArgs& b, T* v, const T* f, T* vold, const l
                           cudaStream_t st);
 extern int g_max_points, g_max_nblk, g_max_nalb;
 void launch_lanczos_bound(const BatchArgs& b, const double* alphas, const double* betas, int steps,
-                          const double* fnorm2, double* bounds, cudaStream_t st);
+                          const double* fnorm2, double* bounds, double* lanczos_min, cudaStream_t st);
+void launch_first_a0(const BatchArgs& b, const double* lanczos_min, double* bounds, cudaStream_t st);
 
 // ---- DG assembly (k_dg.cu) ----
 void launch_proj_overlap(const BatchArgs& b, const AtomBox* boxes, const double* dtab, const double* A,

@@ -202,6 +202,28 @@ int build_plan(const dgdft_problem* pr, const dgdft_alb_params* prm, Plan& P, st
     d.n_proj_e = ncol;
   }
   if (P.dtab.empty()) P.dtab.push_back(0.0);
+  P.dtab32.assign(P.dtab.begin(), P.dtab.end());
+  P.fatoms.assign(P.boxes.size(), FusedAtomRec{});
+  for (int k = 0; k < M; k++) {
+    ElemDesc& d = P.desc[k];
+    d.tab_off = d.pa_count ? P.boxes[d.pa_begin].toff : 0;
+    d.tab_len = 0;
+    for (int i = 0; i < d.pa_count; i++) {
+      const AtomBox& b = P.boxes[d.pa_begin + i];
+      FusedAtomRec& r = P.fatoms[d.pa_begin + i];
+      for (int q = 0; q < 3; q++) { r.s[q] = b.s[q]; r.l[q] = b.l[q]; }
+      r.toff = b.toff - d.tab_off;
+      r.inv2s2 = float(0.5 / (b.pwidth * b.pwidth));
+      const int npa = pr->n_proj_per_atom;
+      r.c[0] = npa >= 1 ? float(b.gamma[0] * b.ns * b.ns * d.dV) : 0.f;
+      for (int q = 1; q < 4; q++) r.c[q] = npa == 4 ? float(b.gamma[q] * b.np * b.np * d.dV) : 0.f;
+      d.tab_len = std::max(d.tab_len, r.toff + b.l[0] + b.l[1] + b.l[2]);
+    }
+    for (int a = 0; a < 3; a++) {
+      const double g = 2.0 * M_PI / (d.qn[a] * d.h[a]);
+      d.kscale[a] = float(0.5 * g * g / double(d.N));
+    }
+  }
   // offsets
   for (int i = 0; i < kOffKinds; i++) { P.off[i].assign(M, 0); P.tot[i] = 0; }
   P.tot_p = P.tot_pe = 0;
@@ -231,6 +253,8 @@ int build_plan(const dgdft_problem* pr, const dgdft_alb_params* prm, Plan& P, st
         d.face_mask |= 3 << (2 * a);
         d.fmax = std::max(d.fmax, d.NE / d.en[a]);
       }
+    d.gtab_off = P.tot_gtab;
+    P.tot_gtab += (long long)d.pa_count * 4096;
     d.troff = P.tot_tr;
     if (d.face_mask) P.tot_tr += 6LL * 2 * d.n_alb * d.fmax;
     P.max_points = std::max(P.max_points, d.N);
@@ -268,6 +292,11 @@ int build_plan(const dgdft_problem* pr, const dgdft_alb_params* prm, Plan& P, st
       P.hx.groups.push_back(g);
     }
     ShapeGroup& g = P.hx.groups[it->second];
+    if (g.elems.empty()) g.fused_ok = true;
+    if (d.pa_count > kFusedAtomLimit || d.tab_len > kFusedTabLimit) g.fused_ok = false;
+    for (int ai = 0; ai < d.pa_count; ai++)
+      for (int q = 0; q < 3; q++)
+        if (P.boxes[d.pa_begin + ai].l[q] > 16) g.fused_ok = false;   // boxes must fit the 16^3 tables
     g.elems.push_back(k);
     g.n_elems = int(g.elems.size());
     g.max_nblk = std::max(g.max_nblk, d.n_blk);

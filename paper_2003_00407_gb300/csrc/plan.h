@@ -18,10 +18,13 @@ struct Plan {
   std::vector<ElemDesc> desc;
   std::vector<AtomBox> boxes;   // Q boxes of all elements, then E boxes
   std::vector<double> dtab;
+  std::vector<float> dtab32;          // FP32 copy of dtab (fused kernel)
+  std::vector<FusedAtomRec> fatoms;   // parallel to boxes (Q boxes filled)
   HxPlan hx;
   std::vector<long long> off[kOffKinds];
   long long tot[kOffKinds] = {0, 0, 0, 0, 0, 0, 0};
   long long tot_tr = 0;         // face traces
+  long long tot_gtab = 0;       // radial factor tables (floats)
   long long tot_p = 0;          // projections [n_blk][n_proj] per element
   long long tot_pe = 0;         // E-projector overlaps [n_alb][n_proj_e] per element
   long long tot_grid = 0;       // points of all domains
@@ -30,6 +33,9 @@ struct Plan {
   ElemDesc* d_desc = nullptr;
   AtomBox* d_boxes = nullptr;
   double* d_dtab = nullptr;
+  float* d_dtab32 = nullptr;
+  FusedAtomRec* d_fatoms = nullptr;
+  float* d_gtab = nullptr;
   long long* d_off[kOffKinds] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
