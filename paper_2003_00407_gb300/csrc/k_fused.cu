@@ -142,7 +142,7 @@ void launch_build_gtab(const BatchArgs& b, const FusedAtomRec* fatoms, const flo
 constexpr int kFusedThreads = 544;   // 17 warps: y tasks (2 x 17 x 48) = 3 rounds, z tasks (2 x 17 x 32) = 2 rounds
 constexpr int kFusedWarps = kFusedThreads / 32;
 constexpr int kFusedMaxAtoms = 96;
-constexpr int kFusedMaxTab = 2048;   // floats of displacement tables per CTA
+constexpr int kFusedMaxTab = 3072;   // floats of displacement tables (+ 32 x-factors per atom) per CTA
 
 template <int QX, int QY, int QZ> constexpr int fused_smem_bytes() {
   return (QX / 2 + 1) * QY * QZ * 8 + kFusedMaxTab * 4;
@@ -178,49 +178,86 @@ __device__ __forceinline__ GRow load_grow(const float* __restrict__ gatom, int z
   return r;
 }
 
+// Application from the element's radial-factor table (16 factors of this lane's row, loaded as four
+// 128-bit words; zero outside the sphere and the box): buf += g (b0 + b1 i).
+template <int QX, int QY, int QZ>
+__device__ __forceinline__ void atom_rows16_apply(const FusedAtomRec& at, const float* __restrict__ gatom, int zq,
+                                                  const float* tabs, float hx, float* buf, int pitch,
+                                                  const float* coef) {
+  const int lane = threadIdx.x & 31;
+  const int iy = lane & 15, iz = 2 * zq + (lane >> 4);
+  if (!(iy < at.l[1] && iz < at.l[2])) return;
+  const float* tx = tabs + at.toff;
+  const float dx0 = tx[0];
+  const float dy = tx[at.l[0] + iy], dz = tx[at.l[0] + at.l[1] + iz];
+  const float4* g4 = reinterpret_cast<const float4*>(gatom + (iz * 16 + iy) * 16);
+  const float4 q0 = __ldg(g4), q1 = __ldg(g4 + 1), q2 = __ldg(g4 + 2), q3 = __ldg(g4 + 3);
+  const float g[16] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
+  int yy = at.s[1] + iy;
+  if (yy >= QY) yy -= QY;
+  int zz = at.s[2] + iz;
+  if (zz >= QZ) zz -= QZ;
+  float* rbuf = buf + (zz * QY + yy) * pitch;
+  const float b0 = coef[0] + coef[2] * dy + coef[3] * dz + coef[1] * dx0;
+  const float b1 = coef[1] * hx;
+  const bool nowrap = at.s[0] + 16 <= QX;
+#pragma unroll
+  for (int i = 0; i < 16; i++) {
+    int xx = at.s[0] + i;
+    if (!nowrap && xx >= QX) xx -= QX;
+    if (g[i] != 0.f) atomicAdd(rbuf + xx, g[i] * fmaf(b1, float(i), b0));
+  }
+}
+
+// xf: per-atom x factors in shared memory: xf[i] = exp(-dx_i^2 / 2 sigma^2) and xf[16 + i] = dx_i^2 / rc^2
+// (0 and 1e30 for i beyond the box), so g = e_row xf[i] max(0, rem_row - xf[16 + i])^3.
 template <int QX, int QY, int QZ, bool PROJ>
-__device__ __forceinline__ void atom_rows16(const FusedAtomRec& at, const GRow& gr, int zq, const float* tabs,
-                                            float* buf, int pitch, const float* coef, float acc[4]) {
+__device__ __forceinline__ void atom_rows16(const FusedAtomRec& at, const float* xf, int zq, const float* tabs,
+                                            float hx, float inv_rc2, float* buf, int pitch, const float* coef,
+                                            float acc[4]) {
   const int lane = threadIdx.x & 31;
   const int iy = lane & 15, iz = 2 * zq + (lane >> 4);
   const float* tx = tabs + at.toff;
-  const bool row_ok = iy < at.l[1] && iz < at.l[2];
-  float s = 0.f, sx = 0.f;
+  float s = 0.f, si = 0.f;
   float dy = 0.f, dz = 0.f;
+  const float dx0 = tx[0];   // box displacements are affine: dx_i = dx0 + i hx
+  bool row_ok = iy < at.l[1] && iz < at.l[2];
   if (row_ok) {
     dy = tx[at.l[0] + iy];
     dz = tx[at.l[0] + at.l[1] + iz];
-    const float g[16] = {gr.q[0].x, gr.q[0].y, gr.q[0].z, gr.q[0].w, gr.q[1].x, gr.q[1].y, gr.q[1].z, gr.q[1].w,
-                         gr.q[2].x, gr.q[2].y, gr.q[2].z, gr.q[2].w, gr.q[3].x, gr.q[3].y, gr.q[3].z, gr.q[3].w};
+  }
+  const float dyz2 = dy * dy + dz * dz;
+  const float rem = 1.f - dyz2 * inv_rc2;
+  row_ok = row_ok && rem > 0.f;
+  if (row_ok) {
+    const float erow = __expf(-dyz2 * at.inv2s2);
     int yy = at.s[1] + iy;
     if (yy >= QY) yy -= QY;
     int zz = at.s[2] + iz;
     if (zz >= QZ) zz -= QZ;
     float* rbuf = buf + (zz * QY + yy) * pitch;
-    const float base = PROJ ? 0.f : coef[0] + coef[2] * dy + coef[3] * dz;
-    const int nx = at.l[0];
-    const int hrot = lane >> 4;   // lanes 16-31 visit point (i + 1) % 16 at step i: the two half-warps then
-                                  // touch banks of opposite parity (rows are 2 HX floats apart)
+    // nonlocal term g (c_s + c_x dx + c_y dy + c_z dz) = g (b0 + b1 i)
+    const float b0 = PROJ ? 0.f : erow * (coef[0] + coef[2] * dy + coef[3] * dz + coef[1] * dx0);
+    const float b1 = PROJ ? 0.f : erow * coef[1] * hx;
+    const bool nowrap = at.s[0] + 16 <= QX;
 #pragma unroll
     for (int i = 0; i < 16; i++) {
-      const int ip = hrot ? ((i + 1) & 15) : i;
-      const float gi = hrot ? g[(i + 1) & 15] : g[i];
-      if (ip < nx) {
-        int xx = at.s[0] + ip;
-        if (xx >= QX) xx -= QX;
-        const float dx = tx[ip];
-        if (PROJ) {
-          const float gy = gi * rbuf[xx];
-          s += gy;
-          sx += gy * dx;
-        } else if (gi != 0.f) {
-          atomicAdd(rbuf + xx, gi * fmaf(coef[1], dx, base));
-        }
+      int xx = at.s[0] + i;
+      if (!nowrap && xx >= QX) xx -= QX;
+      const float u = fmaxf(rem - xf[16 + i], 0.f);
+      const float g = xf[i] * u * u * u;
+      if (PROJ) {
+        const float gy = g * rbuf[xx];
+        s += gy;
+        si = fmaf(gy, float(i), si);
+      } else if (g != 0.f) {
+        atomicAdd(rbuf + xx, g * fmaf(b1, float(i), b0));
       }
     }
+    if (PROJ) { s *= erow; si *= erow; }
   }
   if (PROJ) {
-    float sy = s * dy, sz = s * dz;
+    float sx = fmaf(dx0, s, hx * si), sy = s * dy, sz = s * dz;   // sum g y dx = dx0 s + hx sum i g y
     for (int o = 16; o > 0; o >>= 1) {
       s += __shfl_xor_sync(0xffffffffu, s, o);
       sx += __shfl_xor_sync(0xffffffffu, sx, o);
@@ -273,12 +310,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     for (int i = threadIdx.x; i < kFusedMaxAtoms * 4; i += blockDim.x) (&pacc[0][0])[i] = 0.f;
   }
   __syncthreads();
+  float* xfac = tabs + d.tab_len;   // [na][32]
+  for (int i = threadIdx.x; i < na * 32; i += blockDim.x) {
+    const int ai = i >> 5, j = i & 31, ix = j & 15;
+    const FusedAtomRec& at = atoms[ai];
+    const float dx = tabs[at.toff] + float(ix) * float(d.h[0]);
+    const bool in = ix < at.l[0];
+    xfac[i] = j < 16 ? (in ? __expf(-dx * dx * at.inv2s2) : 0.f) : (in ? dx * dx * a.inv_rc2 : 1e30f);
+  }
   if (threadIdx.x == 0) {
     item_off[0] = 0;
     for (int ai = 0; ai < na; ai++) item_off[ai + 1] = item_off[ai] + (atoms[ai].l[2] + 1) / 2;
   }
   const float inv_rc2 = a.inv_rc2;
   const float hy = float(d.h[1]);
+  const float hx = float(d.h[0]);
   const long long vbase = a.xo[k] + (long long)v * (QX * QY * QZ);
   const float4* y4 = reinterpret_cast<const float4*>(Y + vbase);
 
@@ -293,28 +339,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   }
   __syncthreads();
   const int n_items = item_off[na];
-  // ---- phase 1b: projector overlaps <b, y> from the real rows (next item's factors prefetched) ----
+  // ---- phase 1b: projector overlaps <b, y> from the real rows ----
   {
     int ai = 0;
-    int it = warp;
-    GRow cur;
-    if (it < n_items) {
+    for (int it = warp; it < n_items; it += kFusedWarps) {
       while (item_off[ai + 1] <= it) ai++;
-      cur = load_grow(a.gtab + d.gtab_off + (long long)ai * 4096, it - item_off[ai]);
-    }
-    for (; it < n_items; it += kFusedWarps) {
-      const int zq = it - item_off[ai];
-      const int cai = ai;
-      const int nit = it + kFusedWarps;
-      GRow nxt;
-      if (nit < n_items) {
-        while (item_off[ai + 1] <= nit) ai++;
-        nxt = load_grow(a.gtab + d.gtab_off + (long long)ai * 4096, nit - item_off[ai]);
-      }
       float acc[4];
-      atom_rows16<QX, QY, QZ, true>(atoms[cai], cur, zq, tabs, Sf, PITCH, nullptr, acc);
-      if (lane < 4) atomicAdd(&pacc[cai][lane], lane == 0 ? acc[0] : lane == 1 ? acc[1] : lane == 2 ? acc[2] : acc[3]);
-      cur = nxt;
+      atom_rows16<QX, QY, QZ, true>(atoms[ai], xfac + ai * 32, it - item_off[ai], tabs, hx, inv_rc2, Sf, PITCH,
+                                    nullptr, acc);
+      if (lane < 4) atomicAdd(&pacc[ai][lane], lane == 0 ? acc[0] : lane == 1 ? acc[1] : lane == 2 ? acc[2] : acc[3]);
     }
   }
   __syncthreads();
@@ -415,26 +448,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     for (int j = 0; j < QX / 2; j++) srow[j] = zc[j];
   }
   __syncthreads();
-  // ---- phase 5b: nonlocal application ((atom, z-slice pair) items, shared atomics, prefetched factors) ----
+  // ---- phase 5b: nonlocal application ((atom, z-slice pair) items, shared atomics) ----
   {
     int ai = 0;
-    int it = warp;
-    GRow cur;
-    if (it < n_items) {
+    for (int it = warp; it < n_items; it += kFusedWarps) {
       while (item_off[ai + 1] <= it) ai++;
-      cur = load_grow(a.gtab + d.gtab_off + (long long)ai * 4096, it - item_off[ai]);
-    }
-    for (; it < n_items; it += kFusedWarps) {
-      const int zq = it - item_off[ai];
-      const int cai = ai;
-      const int nit = it + kFusedWarps;
-      GRow nxt;
-      if (nit < n_items) {
-        while (item_off[ai + 1] <= nit) ai++;
-        nxt = load_grow(a.gtab + d.gtab_off + (long long)ai * 4096, nit - item_off[ai]);
-      }
-      atom_rows16<QX, QY, QZ, false>(atoms[cai], cur, zq, tabs, Sf, PITCH, pacc[cai], nullptr);
-      cur = nxt;
+      atom_rows16_apply<QX, QY, QZ>(atoms[ai], a.gtab + d.gtab_off + (long long)ai * 4096, it - item_off[ai], tabs,
+                                    hx, Sf, PITCH, pacc[ai]);
     }
   }
   __syncthreads();

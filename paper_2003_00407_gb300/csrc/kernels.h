@@ -11,7 +11,7 @@ constexpr int kTwiddleCount = kMaxLine * (kMaxLine + 1) / 2;
 __host__ __device__ constexpr int twiddle_offset(int n) { return n * (n - 1) / 2; }
 int upload_twiddles(const double2* t64, const float2* t32);
 int upload_fused_twiddles(const float2* t32);
-constexpr int kFusedAtomLimit = 96, kFusedTabLimit = 2048;
+constexpr int kFusedAtomLimit = 96, kFusedTabLimit = 3072;
 
 // Kernel launches issued by this library since it was loaded (reported by dgdft_kernel_launches).
 extern long long g_launches;
