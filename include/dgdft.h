@@ -177,6 +177,29 @@ int dgdft_apply_hamiltonian(dgdft_ctx* ctx, const dgdft_problem* prob, const dgd
 int dgdft_chebyshev_filter(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* params,
                            const double* bounds, const void* X, void* Y, dgdft_stream stream);
 
+/* Allocation-free variant of dgdft_apply_hamiltonian for FP32 blocks
+ * (params.precision must be DGDFT_MIXED): Y = H X with no device allocation at
+ * all, for callers that cannot call cudaMalloc/cudaFree -- hosts whose device
+ * memory is reserved entirely by another allocator, or latency-critical code
+ * that cannot accept the device-wide synchronisation of cudaMalloc/cudaFree.
+ * The paper has no counterpart; it is a deployment aid.
+ *   - No context: every scratch table (element tables, V_eff on Q, projector
+ *     factor tables) is placed in one fixed 24 MiB device array inside the
+ *     library, which every GPU that loads the library holds until exit.  A
+ *     problem that needs more returns DGDFT_UNSUPPORTED (message: the bytes it
+ *     needs) before anything runs; so does a Q shape the fused FP32 kernel does
+ *     not cover.
+ *   - The first call on a device (the current one) looks up the array's device
+ *     address and uploads the FFT twiddles; make that first call before any
+ *     stream capture.
+ *   - All calls share the array and it keeps the last call's contents: calls
+ *     that overlap on the GPU (other streams or host threads) race on it.
+ *   - X, Y and problem->v_extra are caller-owned device buffers laid out as in
+ *     dgdft_apply_hamiltonian; the call synchronises `stream` before returning.
+ *   - Errors are reported by dgdft_last_error(NULL). */
+int dgdft_apply_hamiltonian_noalloc(const dgdft_problem* prob, const dgdft_alb_params* params, const float* X,
+                                    float* Y, dgdft_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,8 @@ FUNCTIONS = {
                                           C.c_void_p, C.c_void_p]),
     "dgdft_chebyshev_filter": (C.c_int, [C.c_void_p, C.POINTER(Problem), C.POINTER(AlbParams), PD, C.c_void_p,
                                          C.c_void_p, C.c_void_p]),
+    "dgdft_apply_hamiltonian_noalloc": (C.c_int, [C.POINTER(Problem), C.POINTER(AlbParams), C.c_void_p, C.c_void_p,
+                                                  C.c_void_p]),
 }
 
 _lib = None

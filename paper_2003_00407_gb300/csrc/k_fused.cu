@@ -507,6 +507,14 @@ static int launch_shape(const ShapeGroup& g, const FusedArgs& a, const float* X,
   return 1;
 }
 
+// 1 when the fused kernel is instantiated for this Q shape.
+int fused_shape_supported(const int qn[3]) {
+  static const int shapes[][3] = {{32, 32, 48}, {16, 16, 16}, {32, 32, 32}, {24, 24, 32}, {24, 24, 48}};
+  for (const auto& s : shapes)
+    if (qn[0] == s[0] && qn[1] == s[1] && qn[2] == s[2]) return 1;
+  return 0;
+}
+
 // Returns 1 when the fused kernel handled the group (FP32, supported shape, fits shared memory).
 int launch_fused_group(const ShapeGroup& g, const HxArgs& h, const float* X, float* Y, const float* Yprev,
                        const float* V, const double* cheb, int cheb_stride, int out_mode, cudaStream_t st) {

@@ -52,6 +52,7 @@ struct HxPlan {
   std::vector<ShapeGroup> groups;
 };
 
+int fused_shape_supported(const int qn[3]);
 // fused FP32 Chebyshev step (k_fused.cu): returns 1 when it handled the group
 int launch_fused_group(const ShapeGroup& g, const HxArgs& h, const float* X, float* Y, const float* Yprev,
                        const float* V, const double* cheb, int cheb_stride, int out_mode, cudaStream_t st);
