@@ -107,20 +107,19 @@ def make_slab(nex, ney, En, Qn, h, n_eig, n_alb, seed, *, n_proj=4, stencil=STEN
 
 
 def electrons_per_element(prob: Problem, per_atom: int = 4) -> np.ndarray:
-    """4 valence electrons (carbon-like) for each atom whose centre lies in E_k."""
+    """4 valence electrons (carbon-like) for each atom whose nearest grid point lies in E_k."""
     M = prob.n_elem
     out = np.zeros(M, dtype=np.float64)
     for k in range(M):
         d = int(prob.elem_dom[k])
+        sel = prob.atom_dom == d
+        if not np.any(sel):
+            continue
         h = prob.dom_h[d]
         n = prob.dom_n[d]
-        for a in range(prob.n_atoms):
-            if int(prob.atom_dom[a]) != d:
-                continue
-            idx = np.floor(prob.atom_pos[a] / h + 0.5).astype(np.int64) % n  # nearest grid point
-            rel = (idx - prob.elem_E0[k]) % n
-            if np.all(rel < prob.elem_En[k]):
-                out[k] += per_atom
+        idx = np.floor(prob.atom_pos[sel] / h + 0.5).astype(np.int64) % n
+        rel = (idx - prob.elem_E0[k]) % n
+        out[k] = per_atom * np.count_nonzero(np.all(rel < prob.elem_En[k], axis=1))
     return out
 
 
