@@ -183,6 +183,22 @@ def config_dict(args, wl):
             "l2": "working set >> L2 (blocks 16 GB per FP32 buffer): no flush needed"}
 
 
+# ------------------------------------------------------------ multi-rank --
+def max_over_ranks(ms, dist, device):
+    """Slowest rank's step time (weak scaling: every rank runs its own replica of the workload)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, n_elem, ms):
+    """Elements/s over all ranks: every rank solves n_elem elements in ms milliseconds at most."""
+    return world * n_elem / (ms / 1000.0)
+
+
 # -------------------------------------------------------------- native arm --
 def run_native(args, wl, rank, world, local_rank):
     import torch
@@ -231,16 +247,12 @@ def run_native(args, wl, rank, world, local_rank):
         stop.record(stream)
         barrier()
     launches = ctx.lib.dgdft_kernel_launches() - launches0
-    ms = start.elapsed_time(stop) / args.steps
+    ms = max_over_ranks(start.elapsed_time(stop) / args.steps, dist, dev)
     t_alb = statistics.mean((start if i == 0 else ends[i - 1]).elapsed_time(mid[i]) for i in range(args.steps))
     t_dg = statistics.mean(mid[i].elapsed_time(ends[i]) for i in range(args.steps))
     iters = res.iters.cpu().numpy()
     status = res.status.cpu().numpy()
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * M / (ms / 1000.0)
+    value = whole_job_value(world, M, ms)
 
     # ---- roofline of the Chebyshev step (FP32 filter), timed live on this stream ----
     roof = filter_roofline(ctx, api, _abi, wl, torch, stream, res)
