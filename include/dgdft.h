@@ -103,7 +103,10 @@ typedef struct {
   const int* n_blk;          /* [M] filter block (n_eig <= n_blk <= 96), or NULL for the
                                 rule n_eig + max(4, ceil(n_eig/10)) rounded up to 8 */
   int cheb_degree;           /* filter order m >= 2 */
-  double tol;                /* residual tolerance ||H x - lambda x|| (dV norm) */
+  double tol;                /* residual tolerance ||H x - lambda x|| (dV norm) of the first n_eig
+                                Ritz pairs: DGDFT_FP64 iterates until every element meets it (else
+                                status NOT_CONVERGED at max_iter); DGDFT_MIXED applies it to the FP32
+                                stage, whose residuals stop at the FP32 rounding floor (see resid) */
   double tol_mixed;          /* DGDFT_MIXED: the FP32 stage stops at this residual or
                                 when FP32 rounding stalls it; 0 = 1e-6 */
   int max_iter;              /* cap on filter passes per precision stage */
@@ -117,7 +120,10 @@ typedef struct {
  * scalars from dgdft_alb_query_sizes; L = max_k n_blk padded as returned. */
 typedef struct {
   double* eigval;   /* [M][L] Ritz values, ascending (first n_blk valid) */
-  double* resid;    /* [M][L] residual norms of the Ritz pairs */
+  double* resid;    /* [M][L] residual norms of the Ritz pairs.  DGDFT_MIXED: those of the final
+                       FP64 Rayleigh-Ritz on the FP32-filtered subspace, at the FP32 rounding floor
+                       (about 2e-5 on 32x32x48 grids); they are made of high-energy components, so
+                       the eigenvalue error is of order resid^2 / ||H||, not resid */
   double* sing;     /* [M][L] singular values of the restricted block (first n_eig) */
   double* coef;     /* [M][L][L] C_k: ALB = Phi_E C_k (first n_eig rows, n_alb cols) */
   double* alb;      /* packed [n_alb][NE] per element: ALB values on E_k, dV-orthonormal */

@@ -150,6 +150,16 @@ def nonlocal_block(ia, ib):
     return out
 
 
+def diagonal_block(prob, k, ik, alpha):
+    """H^DG_kk: kinetic + V_eff + nonlocal + the face terms with test and trial both in E_k."""
+    B0 = ik["kin"] + ik["vmat"] + nonlocal_block(ik, ik)
+    for (axis, side), (val, der) in ik["faces"].items():
+        dA = face_area(prob, k, axis)
+        sgn = 1.0 if side < 0 else -1.0   # k is R on its low face, L on its high face
+        B0 = B0 + dA * (sgn * 0.25 * (val @ der.T + der @ val.T) + alpha * (val @ val.T))
+    return B0
+
+
 def assemble(prob, ingr, alpha):
     """DG blocks [M, n_stencil, max n_alb, max n_alb] (zero padded) and the dropped nonlocal norm."""
     M = prob.n_elem
@@ -159,12 +169,7 @@ def assemble(prob, ingr, alpha):
     for k in range(M):
         ik = ingr[k]
         nk = ik["n_alb"]
-        B0 = ik["kin"] + ik["vmat"] + nonlocal_block(ik, ik)
-        for (axis, side), (val, der) in ik["faces"].items():
-            dA = face_area(prob, k, axis)
-            sgn = 1.0 if side < 0 else -1.0   # k is R on its low face, L on its high face
-            B0 = B0 + dA * (sgn * 0.25 * (val @ der.T + der @ val.T) + alpha * (val @ val.T))
-        blocks[k, 0, :nk, :nk] = B0
+        blocks[k, 0, :nk, :nk] = diagonal_block(prob, k, ik, alpha)
         seen = {k}
         for s in range(1, S):
             kp = int(prob.neighbors[k, s])

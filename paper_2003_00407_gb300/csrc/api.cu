@@ -460,15 +460,15 @@ int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_al
     if ((r = get_stage<float>(ctx, P, s32, 6, u32))) return r;
     launch_random_init<float>(ball, s32.B[0], P.d_off[OFF_X], prm->seed, st);
     if ((r = chefsi_stage<float>(ctx, P, c, s32, prm, degree, lsteps, true, st, res->history))) return r;
-    // final FP64 Rayleigh-Ritz sweep on the FP32 Ritz vectors: X64 in place, HX64 over B1/B2 of the FP32 stage
+    // final FP64 Rayleigh-Ritz sweep on the FP32 Ritz vectors: X64 in place, HX64 over B1/B2 of the FP32 stage.
+    // The FP32 block is orthonormal only to FP32 accuracy; the Rayleigh-Ritz solve takes the Cholesky
+    // factor of its FP64 Gram matrix (generalised problem), so no separate CholQR pass is needed.
     const int u64[4] = {4, 4, 4, 1};
     if ((r = get_stage<double>(ctx, P, s64, 6, u64))) return r;
     launch_set_active(ball, c.flags, st);
     BatchArgs b{P.d_desc, c.flags, P.M};
     const long long* ox = P.d_off[OFF_X];
     launch_convert<float, double>(b, s32.B[0], ox, s64.B[0], ox, NV_BLK, st);
-    // CholQR in FP64 (the FP32 block is orthonormal only to FP32 accuracy), then RR
-    cholqr<double>(P, c, s64.B[0], 1e-13, st);
     rayleigh_ritz<double>(P, c, s64, s64.B[0], st);
     launch_final_resid(b, c.resid2, P.L, c.resid, st);
     X64 = s64.B[0];

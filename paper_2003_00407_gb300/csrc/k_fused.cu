@@ -142,129 +142,188 @@ void launch_build_gtab(const BatchArgs& b, const FusedAtomRec* fatoms, const flo
 constexpr int kFusedThreads = 544;   // 17 warps: y tasks (2 x 17 x 48) = 3 rounds, z tasks (2 x 17 x 32) = 2 rounds
 constexpr int kFusedWarps = kFusedThreads / 32;
 constexpr int kFusedMaxAtoms = 96;
-constexpr int kFusedMaxTab = 3072;   // floats of displacement tables (+ 32 x-factors per atom) per CTA
+constexpr int kFusedMaxTab = 3072;   // floats of displacement and x-factor tables per CTA (at most)
+constexpr int kSmemOptin = 232448;   // opt-in shared memory per block (sm_103)
+constexpr int kFusedStatic = 8192;   // bound on the kernel's static shared memory
 
+// Q shapes with a fused instance: the 32x32x48 sheet elements, small test boxes, and the
+// uneven-batch shapes whose half spectrum fits shared memory (40x40x48, 40x32x48 and 32x40x48
+// do not, and take the multi-pass kernels).
+#define DGDFT_FUSED_SHAPES(X)                                                                      \
+  X(32, 32, 48) X(16, 16, 16) X(32, 32, 32) X(24, 24, 32) X(24, 24, 48) X(40, 32, 32) X(32, 24, 48) \
+  X(24, 32, 32) X(24, 40, 48) X(40, 24, 48) X(40, 40, 32) X(24, 40, 32) X(32, 24, 32) X(24, 32, 48) \
+  X(40, 24, 32) X(32, 40, 32)
+
+template <int QX, int QY, int QZ> constexpr int fused_spectrum_bytes() { return (QX / 2 + 1) * QY * QZ * 8; }
+// displacement-table floats that fit beside the half spectrum
+template <int QX, int QY, int QZ> constexpr int fused_tab_floats() {
+  constexpr int room = (kSmemOptin - kFusedStatic - fused_spectrum_bytes<QX, QY, QZ>()) / 4;
+  return room < kFusedMaxTab ? room : kFusedMaxTab;
+}
 template <int QX, int QY, int QZ> constexpr int fused_smem_bytes() {
-  return (QX / 2 + 1) * QY * QZ * 8 + kFusedMaxTab * 4;
+  static_assert(fused_tab_floats<QX, QY, QZ>() >= 512, "half spectrum too large for shared memory");
+  return fused_spectrum_bytes<QX, QY, QZ>() + fused_tab_floats<QX, QY, QZ>() * 4;
 }
 
-// Nonlocal work item: one z-slice iz of one atom's box, done by one warp.  The
-// slice's x-rows are walked two at a time (lanes 0-15 row A, 16-31 row B; an
-// x-row of a box has at most 16 points), only over the rows whose |dy| can be
-// inside r_cut.  PROJ accumulates the overlap sums (s, x, y, z components
-// without the norms) of the real rows in buf into acc; otherwise the nonlocal
-// term g (c_s + c_x dx + c_y dy + c_z dz) is added into buf.
-// Nonlocal work item: two z-slices (iz = 2 zq + lane/16) of one atom's box; each
-// lane owns one x-row (iy = lane % 16) and its 16 points.  The row's radial
-// factors g come from the element's table (four 128-bit loads, 0 outside the
-// sphere and the box).  PROJ accumulates the overlap sums (s, x, y, z
-// components without the norms) of the real rows in buf into acc; otherwise the
-// nonlocal term g (c_s + c_x dx + c_y dy + c_z dz) is added into buf.
-struct GRow {
-  float4 q[4];
+// Nonlocal work item: two z-slices (iz = 2 zq + h, h = lane / 16) of one atom's box; each
+// lane owns one x-row (iy = lane % 16) and walks its 16 points.  The radial factor is
+// g = exp(-d^2 / 2 sigma^2) (1 - d^2/rc^2)^3 inside r_cut, evaluated as
+// e_row e_x max(R_row - t_x, 0)^3 with e_x = exp(-dx^2 / 2 sigma^2), t_x = dx^2 / rc^2 from the
+// atom's x-factor table (held in registers while the warp stays on the atom),
+// R_row = 1 - (dy^2 + dz^2) / rc^2.  The second half-warp walks the points rotated by one
+// (point j = (i + h) mod 16 at step i): with an even row pitch the two z-slices then fall on
+// odd and even banks, so the row accesses are free of bank conflicts.
+struct NlAtom {
+  float e[16], t[16];   // x factors in the lane's walk order
+};
+struct NlRow {
+  float erow, rem, dy, dz;
+  float* row;           // the row slot in the shared buffer
+  bool ok;
 };
 
-// the 16 radial factors of this lane's x-row of item (atom ai, z-slice pair zq)
-__device__ __forceinline__ GRow load_grow(const float* __restrict__ gatom, int zq) {
-  const int lane = threadIdx.x & 31;
-  const int iy = lane & 15, iz = 2 * zq + (lane >> 4);
-  GRow r;
-  if (iz < 16) {
-    const float4* g4 = reinterpret_cast<const float4*>(gatom + (iz * 16 + iy) * 16);
-    r.q[0] = __ldg(g4); r.q[1] = __ldg(g4 + 1); r.q[2] = __ldg(g4 + 2); r.q[3] = __ldg(g4 + 3);
-  } else {
-    r.q[0] = r.q[1] = r.q[2] = r.q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+__device__ __forceinline__ void nl_atom(const float* xf, NlAtom& x) {
+  const int h = (threadIdx.x & 31) >> 4;
+#pragma unroll
+  for (int i = 0; i < 16; i++) {
+    const int j = (i + h) & 15;
+    x.e[i] = xf[j];
+    x.t[i] = xf[16 + j];
   }
-  return r;
 }
 
-// Application from the element's radial-factor table (16 factors of this lane's row, loaded as four
-// 128-bit words; zero outside the sphere and the box): buf += g (b0 + b1 i).
-template <int QX, int QY, int QZ>
-__device__ __forceinline__ void atom_rows16_apply(const FusedAtomRec& at, const float* __restrict__ gatom, int zq,
-                                                  const float* tabs, float hx, float* buf, int pitch,
-                                                  const float* coef) {
+template <int QY, int QZ>
+__device__ __forceinline__ void nl_row(const FusedAtomRec& at, int zq, const float* tabs, float inv_rc2, float* buf,
+                                       int pitch, NlRow& r) {
   const int lane = threadIdx.x & 31;
-  const int iy = lane & 15, iz = 2 * zq + (lane >> 4);
-  if (!(iy < at.l[1] && iz < at.l[2])) return;
-  const float* tx = tabs + at.toff;
-  const float dx0 = tx[0];
-  const float dy = tx[at.l[0] + iy], dz = tx[at.l[0] + at.l[1] + iz];
-  const float4* g4 = reinterpret_cast<const float4*>(gatom + (iz * 16 + iy) * 16);
-  const float4 q0 = __ldg(g4), q1 = __ldg(g4 + 1), q2 = __ldg(g4 + 2), q3 = __ldg(g4 + 3);
-  const float g[16] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
+  const int h = lane >> 4, iy = lane & 15, iz = 2 * zq + h;
+  r.ok = iy < at.l[1] && iz < at.l[2];
+  r.dy = 0.f;
+  r.dz = 0.f;
+  if (r.ok) {
+    r.dy = tabs[at.toff + at.l[0] + iy];
+    r.dz = tabs[at.toff + at.l[0] + at.l[1] + iz];
+  }
+  const float dyz2 = r.dy * r.dy + r.dz * r.dz;
+  r.rem = 1.f - dyz2 * inv_rc2;
+  r.ok = r.ok && r.rem > 0.f;
+  r.erow = r.ok ? __expf(-dyz2 * at.inv2s2) : 0.f;
   int yy = at.s[1] + iy;
   if (yy >= QY) yy -= QY;
   int zz = at.s[2] + iz;
   if (zz >= QZ) zz -= QZ;
-  float* rbuf = buf + (zz * QY + yy) * pitch;
-  const float b0 = coef[0] + coef[2] * dy + coef[3] * dz + coef[1] * dx0;
-  const float b1 = coef[1] * hx;
-  const bool nowrap = at.s[0] + 16 <= QX;
+  r.row = buf + (zz * QY + yy) * pitch;
+}
+
+// Overlap sums of one item (s, x, y, z components without the norms), reduced over the warp:
+// sum g y, sum g y dx (= dx0 sum g y + hx sum j g y), sum g y dy, sum g y dz.
+template <int QX>
+__device__ __forceinline__ void nl_proj(const FusedAtomRec& at, const NlAtom& x, const NlRow& r, float dx0,
+                                        float hx, float acc[4]) {
+  const int h = (threadIdx.x & 31) >> 4;
+  float s = 0.f, si = 0.f;
+  if (r.ok) {
+    if (at.s[0] + 17 <= QX) {
+      // no wrap: point i < 15 of the walk sits at base[i]; the last one at base[15] or row[s]
+      const float* base = r.row + at.s[0] + h;
 #pragma unroll
-  for (int i = 0; i < 16; i++) {
-    int xx = at.s[0] + i;
-    if (!nowrap && xx >= QX) xx -= QX;
-    if (g[i] != 0.f) atomicAdd(rbuf + xx, g[i] * fmaf(b1, float(i), b0));
+      for (int i = 0; i < 15; i++) {
+        const float u = fmaxf(r.rem - x.t[i], 0.f);
+        const float gy = x.e[i] * (u * u * u) * base[i];
+        s += gy;
+        si = fmaf(gy, float(i), si);
+      }
+      si = fmaf(float(h), s, si);
+      const float u = fmaxf(r.rem - x.t[15], 0.f);
+      const float gy = x.e[15] * (u * u * u) * (h ? r.row[at.s[0]] : base[15]);
+      s += gy;
+      si = fmaf(gy, h ? 0.f : 15.f, si);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const int j = (i + h) & 15;
+        int xx = at.s[0] + j;
+        if (xx >= QX) xx -= QX;
+        const float u = fmaxf(r.rem - x.t[i], 0.f);
+        const float gy = x.e[i] * (u * u * u) * r.row[xx];
+        s += gy;
+        si = fmaf(gy, float(j), si);
+      }
+    }
+    s *= r.erow;
+    si *= r.erow;
+  }
+  float sx = fmaf(dx0, s, hx * si), sy = s * r.dy, sz = s * r.dz;
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    sz += __shfl_xor_sync(0xffffffffu, sz, o);
+  }
+  acc[0] = s; acc[1] = sx; acc[2] = sy; acc[3] = sz;
+}
+
+// Application of one item: row += g (c_s + c_x dx + c_y dy + c_z dz) = g (b0 + b1 j).
+template <int QX>
+__device__ __forceinline__ void nl_apply(const FusedAtomRec& at, const NlAtom& x, const NlRow& r, float dx0,
+                                         float hx, const float* coef) {
+  if (!r.ok) return;
+  const int h = (threadIdx.x & 31) >> 4;
+  const float b0 = r.erow * (coef[0] + coef[2] * r.dy + coef[3] * r.dz + coef[1] * dx0);
+  const float b1 = r.erow * coef[1] * hx;
+  if (at.s[0] + 17 <= QX) {
+    float* base = r.row + at.s[0] + h;
+    const float b0h = fmaf(b1, float(h), b0);
+#pragma unroll
+    for (int i = 0; i < 15; i++) {
+      const float u = fmaxf(r.rem - x.t[i], 0.f);
+      const float g = x.e[i] * (u * u * u);
+      if (g != 0.f) atomicAdd(base + i, g * fmaf(b1, float(i), b0h));
+    }
+    const float u = fmaxf(r.rem - x.t[15], 0.f);
+    const float g = x.e[15] * (u * u * u);
+    if (g != 0.f) atomicAdd(h ? r.row + at.s[0] : base + 15, g * (h ? b0 : fmaf(b1, 15.f, b0)));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      const int j = (i + h) & 15;
+      int xx = at.s[0] + j;
+      if (xx >= QX) xx -= QX;
+      const float u = fmaxf(r.rem - x.t[i], 0.f);
+      const float g = x.e[i] * (u * u * u);
+      if (g != 0.f) atomicAdd(r.row + xx, g * fmaf(b1, float(j), b0));
+    }
   }
 }
 
-// xf: per-atom x factors in shared memory: xf[i] = exp(-dx_i^2 / 2 sigma^2) and xf[16 + i] = dx_i^2 / rc^2
-// (0 and 1e30 for i beyond the box), so g = e_row xf[i] max(0, rem_row - xf[16 + i])^3.
+// All nonlocal items of the CTA: warp w takes a contiguous range of items, so it mostly stays
+// on one atom and loads that atom's x factors once.
 template <int QX, int QY, int QZ, bool PROJ>
-__device__ __forceinline__ void atom_rows16(const FusedAtomRec& at, const float* xf, int zq, const float* tabs,
-                                            float hx, float inv_rc2, float* buf, int pitch, const float* coef,
-                                            float acc[4]) {
-  const int lane = threadIdx.x & 31;
-  const int iy = lane & 15, iz = 2 * zq + (lane >> 4);
-  const float* tx = tabs + at.toff;
-  float s = 0.f, si = 0.f;
-  float dy = 0.f, dz = 0.f;
-  const float dx0 = tx[0];   // box displacements are affine: dx_i = dx0 + i hx
-  bool row_ok = iy < at.l[1] && iz < at.l[2];
-  if (row_ok) {
-    dy = tx[at.l[0] + iy];
-    dz = tx[at.l[0] + at.l[1] + iz];
-  }
-  const float dyz2 = dy * dy + dz * dz;
-  const float rem = 1.f - dyz2 * inv_rc2;
-  row_ok = row_ok && rem > 0.f;
-  if (row_ok) {
-    const float erow = __expf(-dyz2 * at.inv2s2);
-    int yy = at.s[1] + iy;
-    if (yy >= QY) yy -= QY;
-    int zz = at.s[2] + iz;
-    if (zz >= QZ) zz -= QZ;
-    float* rbuf = buf + (zz * QY + yy) * pitch;
-    // nonlocal term g (c_s + c_x dx + c_y dy + c_z dz) = g (b0 + b1 i)
-    const float b0 = PROJ ? 0.f : erow * (coef[0] + coef[2] * dy + coef[3] * dz + coef[1] * dx0);
-    const float b1 = PROJ ? 0.f : erow * coef[1] * hx;
-    const bool nowrap = at.s[0] + 16 <= QX;
-#pragma unroll
-    for (int i = 0; i < 16; i++) {
-      int xx = at.s[0] + i;
-      if (!nowrap && xx >= QX) xx -= QX;
-      const float u = fmaxf(rem - xf[16 + i], 0.f);
-      const float g = xf[i] * u * u * u;
-      if (PROJ) {
-        const float gy = g * rbuf[xx];
-        s += gy;
-        si = fmaf(gy, float(i), si);
-      } else if (g != 0.f) {
-        atomicAdd(rbuf + xx, g * fmaf(b1, float(i), b0));
-      }
+__device__ __forceinline__ void nl_phase(const FusedAtomRec* atoms, const int* item_off, int na, const float* xfac,
+                                         const float* tabs, float inv_rc2, float hx, float* buf, int pitch,
+                                         float (*pacc)[4]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_items = item_off[na];
+  const int it0 = (n_items * warp) / kFusedWarps, it1 = (n_items * (warp + 1)) / kFusedWarps;
+  int ai = 0, cur = -1;
+  NlAtom x;
+  for (int it = it0; it < it1; it++) {
+    while (item_off[ai + 1] <= it) ai++;
+    if (ai != cur) {
+      nl_atom(xfac + ai * 32, x);
+      cur = ai;
     }
-    if (PROJ) { s *= erow; si *= erow; }
-  }
-  if (PROJ) {
-    float sx = fmaf(dx0, s, hx * si), sy = s * dy, sz = s * dz;   // sum g y dx = dx0 s + hx sum i g y
-    for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_xor_sync(0xffffffffu, s, o);
-      sx += __shfl_xor_sync(0xffffffffu, sx, o);
-      sy += __shfl_xor_sync(0xffffffffu, sy, o);
-      sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    const FusedAtomRec& at = atoms[ai];
+    NlRow r;
+    nl_row<QY, QZ>(at, it - item_off[ai], tabs, inv_rc2, buf, pitch, r);
+    const float dx0 = tabs[at.toff];   // box displacements are affine: dx_j = dx0 + j hx
+    if (PROJ) {
+      float acc[4];
+      nl_proj<QX>(at, x, r, dx0, hx, acc);
+      if (lane < 4) atomicAdd(&pacc[ai][lane], lane == 0 ? acc[0] : lane == 1 ? acc[1] : lane == 2 ? acc[2] : acc[3]);
+    } else {
+      nl_apply<QX>(at, x, r, dx0, hx, pacc[ai]);
     }
-    acc[0] = s; acc[1] = sx; acc[2] = sy; acc[3] = sz;
   }
 }
 
@@ -310,7 +369,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     for (int i = threadIdx.x; i < kFusedMaxAtoms * 4; i += blockDim.x) (&pacc[0][0])[i] = 0.f;
   }
   __syncthreads();
-  float* xfac = tabs + d.tab_len;   // [na][32]
+  float* xfac = tabs + d.tab_len;   // [na][32]: e_x (0 beyond the box), then t_x (1e30 beyond the box)
   for (int i = threadIdx.x; i < na * 32; i += blockDim.x) {
     const int ai = i >> 5, j = i & 31, ix = j & 15;
     const FusedAtomRec& at = atoms[ai];
@@ -323,33 +382,36 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     for (int ai = 0; ai < na; ai++) item_off[ai + 1] = item_off[ai] + (atoms[ai].l[2] + 1) / 2;
   }
   const float inv_rc2 = a.inv_rc2;
-  const float hy = float(d.h[1]);
   const float hx = float(d.h[0]);
   const long long vbase = a.xo[k] + (long long)v * (QX * QY * QZ);
   const float4* y4 = reinterpret_cast<const float4*>(Y + vbase);
 
-  // ---- phase 1a: the real vector into the row slots (coalesced float4 loads) ----
-#pragma unroll 4
-  for (int i = threadIdx.x; i < NF4; i += kFusedThreads) {
-    const int r = i / (QX / 4), c = i % (QX / 4);
-    const float4 q = __ldg(y4 + i);
-    float2* dst = reinterpret_cast<float2*>(Sf + r * PITCH + 4 * c);
-    dst[0] = make_float2(q.x, q.y);
-    dst[1] = make_float2(q.z, q.w);
-  }
-  __syncthreads();
-  const int n_items = item_off[na];
-  // ---- phase 1b: projector overlaps <b, y> from the real rows ----
+  // ---- phase 1a: the real vector into the row slots (coalesced float4 loads, 8 in flight per thread) ----
   {
-    int ai = 0;
-    for (int it = warp; it < n_items; it += kFusedWarps) {
-      while (item_off[ai + 1] <= it) ai++;
-      float acc[4];
-      atom_rows16<QX, QY, QZ, true>(atoms[ai], xfac + ai * 32, it - item_off[ai], tabs, hx, inv_rc2, Sf, PITCH,
-                                    nullptr, acc);
-      if (lane < 4) atomicAdd(&pacc[ai][lane], lane == 0 ? acc[0] : lane == 1 ? acc[1] : lane == 2 ? acc[2] : acc[3]);
+    constexpr int NIT = (NF4 + kFusedThreads - 1) / kFusedThreads;
+#pragma unroll
+    for (int b0 = 0; b0 < NIT; b0 += 8) {
+      float4 q[8];
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const int i = threadIdx.x + (b0 + u) * kFusedThreads;
+        if (b0 + u < NIT && i < NF4) q[u] = __ldg(y4 + i);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const int i = threadIdx.x + (b0 + u) * kFusedThreads;
+        if (b0 + u < NIT && i < NF4) {
+          const int r = i / (QX / 4), c = i % (QX / 4);
+          float2* dst = reinterpret_cast<float2*>(Sf + r * PITCH + 4 * c);
+          dst[0] = make_float2(q[u].x, q[u].y);
+          dst[1] = make_float2(q[u].z, q[u].w);
+        }
+      }
     }
   }
+  __syncthreads();
+  // ---- phase 1b: projector overlaps <b, y> from the real rows ----
+  nl_phase<QX, QY, QZ, true>(atoms, item_off, na, xfac, tabs, inv_rc2, hx, Sf, PITCH, pacc);
   __syncthreads();
   // ---- phase 1c: R2C along x in each row slot: z = x_even + i x_odd, X_k = E_k + w^k O_k ----
   for (int r = threadIdx.x; r < NROW; r += blockDim.x) {
@@ -449,14 +511,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   }
   __syncthreads();
   // ---- phase 5b: nonlocal application ((atom, z-slice pair) items, shared atomics) ----
-  {
-    int ai = 0;
-    for (int it = warp; it < n_items; it += kFusedWarps) {
-      while (item_off[ai + 1] <= it) ai++;
-      atom_rows16_apply<QX, QY, QZ>(atoms[ai], a.gtab + d.gtab_off + (long long)ai * 4096, it - item_off[ai], tabs,
-                                    hx, Sf, PITCH, pacc[ai]);
-    }
-  }
+  nl_phase<QX, QY, QZ, false>(atoms, item_off, na, xfac, tabs, inv_rc2, hx, Sf, PITCH, pacc);
   __syncthreads();
   // ---- phase 5c: V y, Chebyshev combination, store (coalesced float4) ----
   float alpha = 1.f, shift = 0.f, beta = 0.f;
@@ -469,24 +524,40 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   const float4* p4 = (out_mode == OUT_CHEB && Yprev != nullptr && beta != 0.f)
                          ? reinterpret_cast<const float4*>(Yprev + vbase) : nullptr;
   float4* o4 = reinterpret_cast<float4*>(Yout + vbase);
-#pragma unroll 4
-  for (int i = threadIdx.x; i < NF4; i += kFusedThreads) {
-    const int r = i / (QX / 4), c = i % (QX / 4);
-    const float2* tr = reinterpret_cast<const float2*>(Sf + r * PITCH + 4 * c);
-    const float2 t0 = tr[0], t1 = tr[1];
-    const float4 yy = __ldg(y4 + i), vv = __ldg(v4 + i);
-    float4 h = {t0.x + vv.x * yy.x, t0.y + vv.y * yy.y, t1.x + vv.z * yy.z, t1.y + vv.w * yy.w};
-    if (out_mode == OUT_CHEB) {
-      h.x = alpha * (h.x - shift * yy.x);
-      h.y = alpha * (h.y - shift * yy.y);
-      h.z = alpha * (h.z - shift * yy.z);
-      h.w = alpha * (h.w - shift * yy.w);
-      if (p4 != nullptr) {
-        const float4 pp = __ldg(p4 + i);
-        h.x += beta * pp.x; h.y += beta * pp.y; h.z += beta * pp.z; h.w += beta * pp.w;
+  {
+    // 4 chunks in flight per thread: y and V (L2), y_prev (HBM), then the combination and the store
+    constexpr int NIT = (NF4 + kFusedThreads - 1) / kFusedThreads;
+#pragma unroll
+    for (int b0 = 0; b0 < NIT; b0 += 4) {
+      float4 yy[4], vv[4], pp[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int i = threadIdx.x + (b0 + u) * kFusedThreads;
+        if (b0 + u < NIT && i < NF4) {
+          yy[u] = __ldg(y4 + i);
+          vv[u] = __ldg(v4 + i);
+          pp[u] = p4 != nullptr ? __ldg(p4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int i = threadIdx.x + (b0 + u) * kFusedThreads;
+        if (b0 + u < NIT && i < NF4) {
+          const int r = i / (QX / 4), c = i % (QX / 4);
+          const float2* tr = reinterpret_cast<const float2*>(Sf + r * PITCH + 4 * c);
+          const float2 t0 = tr[0], t1 = tr[1];
+          float4 h = {t0.x + vv[u].x * yy[u].x, t0.y + vv[u].y * yy[u].y, t1.x + vv[u].z * yy[u].z,
+                      t1.y + vv[u].w * yy[u].w};
+          if (out_mode == OUT_CHEB) {
+            h.x = alpha * (h.x - shift * yy[u].x) + beta * pp[u].x;
+            h.y = alpha * (h.y - shift * yy[u].y) + beta * pp[u].y;
+            h.z = alpha * (h.z - shift * yy[u].z) + beta * pp[u].z;
+            h.w = alpha * (h.w - shift * yy[u].w) + beta * pp[u].w;
+          }
+          o4[i] = h;
+        }
       }
     }
-    o4[i] = h;
   }
 }
 
@@ -507,13 +578,17 @@ static int launch_shape(const ShapeGroup& g, const FusedArgs& a, const float* X,
   return 1;
 }
 
-// 1 when the fused kernel is instantiated for this Q shape.
-int fused_shape_supported(const int qn[3]) {
-  static const int shapes[][3] = {{32, 32, 48}, {16, 16, 16}, {32, 32, 32}, {24, 24, 32}, {24, 24, 48}};
-  for (const auto& s : shapes)
-    if (qn[0] == s[0] && qn[1] == s[1] && qn[2] == s[2]) return 1;
+// Displacement-table capacity (floats) of the fused instance for this Q shape; 0 = no instance.
+int fused_tab_capacity(const int qn[3]) {
+#define DGDFT_CAP(a, b, c) \
+  if (qn[0] == a && qn[1] == b && qn[2] == c) return fused_tab_floats<a, b, c>();
+  DGDFT_FUSED_SHAPES(DGDFT_CAP)
+#undef DGDFT_CAP
   return 0;
 }
+
+// 1 when the fused kernel is instantiated for this Q shape.
+int fused_shape_supported(const int qn[3]) { return fused_tab_capacity(qn) > 0; }
 
 // Returns 1 when the fused kernel handled the group (FP32, supported shape, fits shared memory).
 int launch_fused_group(const ShapeGroup& g, const HxArgs& h, const float* X, float* Y, const float* Yprev,
@@ -530,11 +605,10 @@ int launch_fused_group(const ShapeGroup& g, const HxArgs& h, const float* X, flo
   a.npa = h.n_proj_per_atom;
   a.inv_rc2 = float(1.0 / (h.r_cut * h.r_cut));
   int done = 0;
-  done = done || launch_shape<32, 32, 48>(g, a, X, Y, Yprev, V, cheb, cheb_stride, out_mode, st);
-  done = done || launch_shape<16, 16, 16>(g, a, X, Y, Yprev, V, cheb, cheb_stride, out_mode, st);
-  done = done || launch_shape<32, 32, 32>(g, a, X, Y, Yprev, V, cheb, cheb_stride, out_mode, st);
-  done = done || launch_shape<24, 24, 32>(g, a, X, Y, Yprev, V, cheb, cheb_stride, out_mode, st);
-  done = done || launch_shape<24, 24, 48>(g, a, X, Y, Yprev, V, cheb, cheb_stride, out_mode, st);
+#define DGDFT_LAUNCH(qx, qy, qz) \
+  done = done || launch_shape<qx, qy, qz>(g, a, X, Y, Yprev, V, cheb, cheb_stride, out_mode, st);
+  DGDFT_FUSED_SHAPES(DGDFT_LAUNCH)
+#undef DGDFT_LAUNCH
   return done;
 }
 

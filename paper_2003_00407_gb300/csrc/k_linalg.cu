@@ -9,7 +9,6 @@
 namespace dgdft {
 
 constexpr int kMaxN = 96;       // largest filter block handled by the small kernels
-constexpr int kGramKT = 32;     // points per Gram tile
 
 __device__ __forceinline__ int count_of(const ElemDesc& d, int mode) {
   switch (mode) {
@@ -27,180 +26,241 @@ __device__ __forceinline__ bool elem_active(const BatchArgs& b, int k) {
 }
 
 // ---------------------------------------------------------------- Gram ----
-// FP64 inputs accumulate in FP64.  FP32 inputs accumulate each 32-point tile
-// in FP32 registers and add the tile sums into FP64 accumulators.
-template <typename TI>
+// G[i][j] += scale dV sum_p A[i][p] w[p] B[j][p] over one chunk of points per CTA.
+// 16 x 16 threads, each owning an R x R register tile of the (16R)^2 outputs; the points
+// stream through shared memory in tiles of kGramKT.  FP64 inputs accumulate in FP64;
+// FP32 inputs accumulate kGramSub points in FP32 registers, then into FP64 accumulators.
+constexpr int kGramKT = 32;      // points per shared-memory tile
+constexpr int kGramSub = 128;    // points per FP32 partial sum
+constexpr int kGramChunk = 4096; // points per CTA
+template <typename TI, int R>
 __global__ void __launch_bounds__(256) k_gram(BatchArgs b, const TI* __restrict__ A, const long long* ao, int na_mode,
                                               const TI* __restrict__ B, const long long* bo, int nb_mode, int npts_mode,
                                               const double* __restrict__ w, const long long* wo, double* G, int ldg,
-                                              int chunk, double scale) {
+                                              double scale) {
+  constexpr int NT = 16 * R;
   const int k = blockIdx.y;
   if (k >= b.M || !elem_active(b, k)) return;
   const ElemDesc& d = b.desc[k];
   const int na = count_of(d, na_mode), nb = count_of(d, nb_mode), np = count_of(d, npts_mode);
-  const int p_begin = blockIdx.x * chunk;
+  const int p_begin = blockIdx.x * kGramChunk;
   if (p_begin >= np) return;
-  const int p_end = min(np, p_begin + chunk);
-  extern __shared__ __align__(16) unsigned char smem[];
-  TI* sA = reinterpret_cast<TI*>(smem);            // [KT][kMaxN+1]
-  TI* sB = sA + kGramKT * (kMaxN + 1);
+  const int p_end = min(np, p_begin + kGramChunk);
+  __shared__ TI sA[kGramKT][NT + 1];
+  __shared__ TI sB[kGramKT][NT + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[6][6];
+  double acc[R][R];
+  TI part[R][R];
 #pragma unroll
-  for (int r = 0; r < 6; r++)
+  for (int r = 0; r < R; r++)
 #pragma unroll
-    for (int c = 0; c < 6; c++) acc[r][c] = 0.0;
+    for (int c = 0; c < R; c++) { acc[r][c] = 0.0; part[r][c] = TI(0); }
   const TI* Ak = A + ao[k];
   const TI* Bk = B + bo[k];
   const double* wk = w ? w + wo[k] : nullptr;
   for (int p0 = p_begin; p0 < p_end; p0 += kGramKT) {
-    for (int idx = threadIdx.x; idx < na * kGramKT; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < NT * kGramKT; idx += 256) {
       const int i = idx / kGramKT, kk = idx - i * kGramKT;
       const int p = p0 + kk;
-      sA[kk * (kMaxN + 1) + i] = (p < p_end) ? Ak[(long long)i * np + p] : TI(0);
-    }
-    for (int idx = threadIdx.x; idx < nb * kGramKT; idx += blockDim.x) {
-      const int j = idx / kGramKT, kk = idx - j * kGramKT;
-      const int p = p0 + kk;
-      TI v = (p < p_end) ? Bk[(long long)j * np + p] : TI(0);
-      if (wk != nullptr && p < p_end) v = TI(double(v) * wk[p]);
-      sB[kk * (kMaxN + 1) + j] = v;
+      TI va = TI(0), vb = TI(0);
+      if (p < p_end) {
+        if (i < na) va = Ak[(long long)i * np + p];
+        if (i < nb) {
+          vb = Bk[(long long)i * np + p];
+          if (wk != nullptr) vb = TI(double(vb) * wk[p]);
+        }
+      }
+      sA[kk][i] = va;
+      sB[kk][i] = vb;
     }
     __syncthreads();
-    TI part[6][6];
-#pragma unroll
-    for (int r = 0; r < 6; r++)
-#pragma unroll
-      for (int c = 0; c < 6; c++) part[r][c] = TI(0);
-#pragma unroll 4
+#pragma unroll 8
     for (int kk = 0; kk < kGramKT; kk++) {
-      TI av[6], bv[6];
+      TI av[R], bv[R];
 #pragma unroll
-      for (int r = 0; r < 6; r++) av[r] = sA[kk * (kMaxN + 1) + ty + 16 * r];
+      for (int r = 0; r < R; r++) av[r] = sA[kk][ty + 16 * r];
 #pragma unroll
-      for (int c = 0; c < 6; c++) bv[c] = sB[kk * (kMaxN + 1) + tx + 16 * c];
+      for (int c = 0; c < R; c++) bv[c] = sB[kk][tx + 16 * c];
 #pragma unroll
-      for (int r = 0; r < 6; r++)
+      for (int r = 0; r < R; r++)
 #pragma unroll
-        for (int c = 0; c < 6; c++) part[r][c] += av[r] * bv[c];
+        for (int c = 0; c < R; c++) part[r][c] = fma(av[r], bv[c], part[r][c]);
     }
-#pragma unroll
-    for (int r = 0; r < 6; r++)
-#pragma unroll
-      for (int c = 0; c < 6; c++) acc[r][c] += double(part[r][c]);
     __syncthreads();
+    if (((p0 - p_begin + kGramKT) % kGramSub) == 0 || p0 + kGramKT >= p_end) {
+#pragma unroll
+      for (int r = 0; r < R; r++)
+#pragma unroll
+        for (int c = 0; c < R; c++) { acc[r][c] += double(part[r][c]); part[r][c] = TI(0); }
+    }
   }
   double* Gk = G + (long long)k * ldg * ldg;
+  const double f = d.dV * scale;
 #pragma unroll
-  for (int r = 0; r < 6; r++) {
+  for (int r = 0; r < R; r++) {
     const int i = ty + 16 * r;
     if (i >= na) continue;
 #pragma unroll
-    for (int c = 0; c < 6; c++) {
+    for (int c = 0; c < R; c++) {
       const int j = tx + 16 * c;
-      if (j < nb) atomicAdd(&Gk[i * ldg + j], acc[r][c] * d.dV * scale);
+      if (j < nb) atomicAdd(&Gk[i * ldg + j], acc[r][c] * f);
     }
   }
 }
+
+// register tile for n <= 16R outputs per side
+static int tile_r(int n) { return n <= 32 ? 2 : n <= 48 ? 3 : n <= 64 ? 4 : n <= 80 ? 5 : 6; }
 
 template <typename TI>
 void launch_gram(const BatchArgs& b, const TI* A, const long long* ao, int na_mode, const TI* B, const long long* bo,
                  int nb_mode, int npts_mode, const double* weight, const long long* wo, double* G, int ldg,
                  cudaStream_t st, double scale) {
-  // callers zero G first; chunk of points per CTA
-  extern int g_max_points;
-  const int chunk = 1024;
-  dim3 grid((g_max_points + chunk - 1) / chunk, b.M);
-  const int smem = 2 * kGramKT * (kMaxN + 1) * sizeof(TI);
-  count_launch(); k_gram<TI><<<grid, 256, smem, st>>>(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, weight, wo, G, ldg, chunk,
-                                    scale);
+  // callers zero G first
+  extern int g_max_points, g_max_nblk;
+  dim3 grid((g_max_points + kGramChunk - 1) / kGramChunk, b.M);
+  count_launch();
+  switch (tile_r(g_max_nblk)) {
+    case 2: k_gram<TI, 2><<<grid, 256, 0, st>>>(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, weight, wo, G, ldg, scale); break;
+    case 3: k_gram<TI, 3><<<grid, 256, 0, st>>>(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, weight, wo, G, ldg, scale); break;
+    case 4: k_gram<TI, 4><<<grid, 256, 0, st>>>(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, weight, wo, G, ldg, scale); break;
+    case 5: k_gram<TI, 5><<<grid, 256, 0, st>>>(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, weight, wo, G, ldg, scale); break;
+    default: k_gram<TI, 6><<<grid, 256, 0, st>>>(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, weight, wo, G, ldg, scale); break;
+  }
 }
 int g_max_points = 0;
 
 // ------------------------------------------------------------- rotation ----
-// Z[j][p] = sum_i W[i][j] X[i][p], for a chunk of 64 points per CTA; the whole
-// chunk is staged in shared memory first, so Z may alias X.  With X2/Z2 the
-// same W rotates a second block; with theta/resid2 the squared residuals
-// sum_p (Z2[j][p] - theta_j Z[j][p])^2 are accumulated per column.
-constexpr int kRotP = 64;
-template <typename TX, typename TZ>
+// Z[j][p] = sum_i W[i][j] X[i][p] over kRotTiles tiles of 16Q points per CTA; W is staged
+// in shared memory once per CTA and each X tile before any Z of the same points is
+// written, so Z may alias X.  16 x 16 threads: thread (tx, ty) owns outputs
+// j = ty + 16r (r < R) at points tx + 16q (q < Q).  With X2/Z2 the same W rotates a
+// second block; with theta/resid2 the squared residuals sum_p (Z2[j][p] - theta_j Z[j][p])^2
+// are accumulated per column.
+constexpr int kRotTiles = 8;
+template <typename TX, typename TZ, int R, int Q>
 __global__ void __launch_bounds__(256) k_rotate(BatchArgs b, const TX* X, const long long* xo, TZ* Z,
                                                 const long long* zo, int nin_mode, int nout_mode, int npts_mode,
                                                 const double* __restrict__ W, int ldw, const TX* X2, TZ* Z2,
                                                 const double* __restrict__ theta, double* resid2, int ldr) {
-  using TW = TX;
+  constexpr int NT = 16 * R, P = 16 * Q;
   const int k = blockIdx.y;
   if (k >= b.M || !elem_active(b, k)) return;
   const ElemDesc& d = b.desc[k];
   const int nin = count_of(d, nin_mode), nout = count_of(d, nout_mode), np = count_of(d, npts_mode);
-  const int p0 = blockIdx.x * kRotP;
-  if (p0 >= np) return;
+  const int pc0 = blockIdx.x * kRotTiles * P;
+  if (pc0 >= np) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  TW* sW = reinterpret_cast<TW*>(smem);                   // [nin][nout]
-  TX* sX = reinterpret_cast<TX*>(sW + nin * nout);        // [nin][kRotP]
-  TX* sX2 = sX + nin * kRotP;
+  TX* sW = reinterpret_cast<TX*>(smem);     // [nin][NT]
+  TX* sX = sW + nin * NT;                   // [nin][P]
+  TX* sX2 = sX + nin * P;
   const double* Wk = W + (long long)k * ldw * ldw;
-  for (int idx = threadIdx.x; idx < nin * nout; idx += blockDim.x) {
-    const int i = idx / nout, j = idx - i * nout;
-    sW[idx] = TW(Wk[i * ldw + j]);
+  for (int idx = threadIdx.x; idx < nin * NT; idx += 256) {
+    const int i = idx / NT, j = idx - i * NT;
+    sW[idx] = j < nout ? TX(Wk[i * ldw + j]) : TX(0);
   }
   const TX* Xk = X + xo[k];
   const TX* X2k = X2 ? X2 + xo[k] : nullptr;
-  for (int idx = threadIdx.x; idx < nin * kRotP; idx += blockDim.x) {
-    const int i = idx / kRotP, pp = idx - i * kRotP;
-    const int p = p0 + pp;
-    sX[idx] = (p < np) ? Xk[(long long)i * np + p] : TX(0);
-    if (X2k) sX2[idx] = (p < np) ? X2k[(long long)i * np + p] : TX(0);
-  }
-  __syncthreads();
-  const int pp = threadIdx.x & (kRotP - 1), jg = threadIdx.x >> 6;  // 4 column groups
-  TX acc[kMaxN / 4], acc2[kMaxN / 4];
-#pragma unroll
-  for (int r = 0; r < kMaxN / 4; r++) { acc[r] = TX(0); acc2[r] = TX(0); }
-  for (int i = 0; i < nin; i++) {
-    const TX xv = sX[i * kRotP + pp];
-    const TX xv2 = X2k ? sX2[i * kRotP + pp] : TX(0);
-#pragma unroll
-    for (int r = 0; r < kMaxN / 4; r++) {
-      const int j = jg + 4 * r;
-      if (j < nout) {
-        const TW wv = sW[i * nout + j];
-        acc[r] += wv * xv;
-        acc2[r] += wv * xv2;
-      }
-    }
-  }
-  const int p = p0 + pp;
   TZ* Zk = Z + zo[k];
   TZ* Z2k = Z2 ? Z2 + zo[k] : nullptr;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double rsum[R];
 #pragma unroll
-  for (int r = 0; r < kMaxN / 4; r++) {
-    const int j = jg + 4 * r;
-    if (j >= nout) continue;
-    if (p < np) {
-      Zk[(long long)j * np + p] = TZ(acc[r]);
-      if (Z2k) Z2k[(long long)j * np + p] = TZ(acc2[r]);
+  for (int r = 0; r < R; r++) rsum[r] = 0.0;
+  for (int t = 0; t < kRotTiles; t++) {
+    const int p0 = pc0 + t * P;
+    if (p0 >= np) break;
+    __syncthreads();   // previous tile consumed (and W staged)
+    for (int idx = threadIdx.x; idx < nin * P; idx += 256) {
+      const int i = idx / P, pp = idx - i * P;
+      const int p = p0 + pp;
+      sX[idx] = (p < np) ? Xk[(long long)i * np + p] : TX(0);
+      if (X2k) sX2[idx] = (p < np) ? X2k[(long long)i * np + p] : TX(0);
     }
-    if (resid2 != nullptr) {
-      double rr = 0.0;
-      if (p < np) {
-        const double t = double(acc2[r]) - theta[k * ldr + j] * double(acc[r]);
-        rr = t * t;
+    __syncthreads();
+    TX acc[R][Q], acc2[R][Q];
+#pragma unroll
+    for (int r = 0; r < R; r++)
+#pragma unroll
+      for (int q = 0; q < Q; q++) { acc[r][q] = TX(0); acc2[r][q] = TX(0); }
+    if (X2k) {
+      for (int i = 0; i < nin; i++) {
+        TX wv[R], xv[Q], xv2[Q];
+#pragma unroll
+        for (int r = 0; r < R; r++) wv[r] = sW[i * NT + ty + 16 * r];
+#pragma unroll
+        for (int q = 0; q < Q; q++) { xv[q] = sX[i * P + tx + 16 * q]; xv2[q] = sX2[i * P + tx + 16 * q]; }
+#pragma unroll
+        for (int r = 0; r < R; r++)
+#pragma unroll
+          for (int q = 0; q < Q; q++) {
+            acc[r][q] = fma(wv[r], xv[q], acc[r][q]);
+            acc2[r][q] = fma(wv[r], xv2[q], acc2[r][q]);
+          }
       }
-      for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
-      if ((threadIdx.x & 31) == 0) atomicAdd(&resid2[k * ldr + j], rr);
+    } else {
+      for (int i = 0; i < nin; i++) {
+        TX wv[R], xv[Q];
+#pragma unroll
+        for (int r = 0; r < R; r++) wv[r] = sW[i * NT + ty + 16 * r];
+#pragma unroll
+        for (int q = 0; q < Q; q++) xv[q] = sX[i * P + tx + 16 * q];
+#pragma unroll
+        for (int r = 0; r < R; r++)
+#pragma unroll
+          for (int q = 0; q < Q; q++) acc[r][q] = fma(wv[r], xv[q], acc[r][q]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int j = ty + 16 * r;
+      if (j >= nout) continue;
+#pragma unroll
+      for (int q = 0; q < Q; q++) {
+        const int p = p0 + tx + 16 * q;
+        if (p >= np) continue;
+        Zk[(long long)j * np + p] = TZ(acc[r][q]);
+        if (Z2k) Z2k[(long long)j * np + p] = TZ(acc2[r][q]);
+        if (resid2 != nullptr) {
+          const double e = double(acc2[r][q]) - theta[k * ldr + j] * double(acc[r][q]);
+          rsum[r] += e * e;
+        }
+      }
+    }
+  }
+  if (resid2 != nullptr) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      double v = rsum[r];
+      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);   // over tx
+      const int j = ty + 16 * r;
+      if (tx == 0 && j < nout) atomicAdd(&resid2[k * ldr + j], v);
     }
   }
 }
+
+template <typename TX> constexpr int rot_q() { return sizeof(TX) == 4 ? 4 : 2; }
+template <typename TX, int R> constexpr int rot_smem() { return (kMaxN * 16 * R + 2 * kMaxN * 16 * rot_q<TX>()) * sizeof(TX); }
 
 template <typename TX, typename TZ>
 void launch_rotate(const BatchArgs& b, const TX* X, const long long* xo, TZ* Z, const long long* zo, int nin_mode,
                    int nout_mode, int npts_mode, const double* W, int ldw, const TX* X2, TZ* Z2, const double* theta,
                    double* resid2, int ldr, cudaStream_t st) {
-  dim3 grid((g_max_points + kRotP - 1) / kRotP, b.M);
-  const int smem = kMaxN * kMaxN * sizeof(TX) + 2 * kMaxN * kRotP * sizeof(TX);
-  count_launch(); k_rotate<TX, TZ><<<grid, 256, smem, st>>>(b, X, xo, Z, zo, nin_mode, nout_mode, npts_mode, W, ldw, X2, Z2, theta,
-                                            resid2, ldr);
+  constexpr int Q = rot_q<TX>();
+  const int pts = kRotTiles * 16 * Q;
+  dim3 grid((g_max_points + pts - 1) / pts, b.M);
+  extern int g_max_nblk;
+  count_launch();
+#define DGDFT_ROT(RR)                                                                                      \
+  k_rotate<TX, TZ, RR, Q><<<grid, 256, rot_smem<TX, RR>(), st>>>(b, X, xo, Z, zo, nin_mode, nout_mode, npts_mode, \
+                                                               W, ldw, X2, Z2, theta, resid2, ldr)
+  switch (tile_r(g_max_nblk)) {
+    case 2: DGDFT_ROT(2); break;
+    case 3: DGDFT_ROT(3); break;
+    case 4: DGDFT_ROT(4); break;
+    case 5: DGDFT_ROT(5); break;
+    default: DGDFT_ROT(6); break;
+  }
+#undef DGDFT_ROT
 }
 
 // -------------------------------------------------- small dense solvers ----
@@ -506,10 +566,12 @@ void launch_svd_small(const BatchArgs& b, const double* G, double* C, double* si
 
 int set_linalg_smem_limits() {
   int e = 0;
-  e |= allow_max_smem(k_gram<float>);
-  e |= allow_max_smem(k_gram<double>);
-  e |= allow_max_smem(k_rotate<float, float>);
-  e |= allow_max_smem(k_rotate<double, double>);
+  e |= allow_max_smem(k_rotate<float, float, 2, 4>) | allow_max_smem(k_rotate<float, float, 3, 4>);
+  e |= allow_max_smem(k_rotate<float, float, 4, 4>) | allow_max_smem(k_rotate<float, float, 5, 4>);
+  e |= allow_max_smem(k_rotate<float, float, 6, 4>);
+  e |= allow_max_smem(k_rotate<double, double, 2, 2>) | allow_max_smem(k_rotate<double, double, 3, 2>);
+  e |= allow_max_smem(k_rotate<double, double, 4, 2>) | allow_max_smem(k_rotate<double, double, 5, 2>);
+  e |= allow_max_smem(k_rotate<double, double, 6, 2>);
   e |= allow_max_smem(k_chol_inv);
   e |= allow_max_smem(k_rr_small);
   e |= allow_max_smem(k_svd_small);

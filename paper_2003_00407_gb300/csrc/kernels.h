@@ -11,7 +11,7 @@ constexpr int kTwiddleCount = kMaxLine * (kMaxLine + 1) / 2;
 __host__ __device__ constexpr int twiddle_offset(int n) { return n * (n - 1) / 2; }
 int upload_twiddles(const double2* t64, const float2* t32);
 int upload_fused_twiddles(const float2* t32);
-constexpr int kFusedAtomLimit = 96, kFusedTabLimit = 3072;
+constexpr int kFusedAtomLimit = 96;
 
 // Kernel launches issued by this library since it was loaded (reported by dgdft_kernel_launches).
 extern long long g_launches;
@@ -53,6 +53,7 @@ struct HxPlan {
 };
 
 int fused_shape_supported(const int qn[3]);
+int fused_tab_capacity(const int qn[3]);
 // fused FP32 Chebyshev step (k_fused.cu): returns 1 when it handled the group
 int launch_fused_group(const ShapeGroup& g, const HxArgs& h, const float* X, float* Y, const float* Yprev,
                        const float* V, const double* cheb, int cheb_stride, int out_mode, cudaStream_t st);

@@ -293,7 +293,7 @@ int build_plan(const dgdft_problem* pr, const dgdft_alb_params* prm, Plan& P, st
     }
     ShapeGroup& g = P.hx.groups[it->second];
     if (g.elems.empty()) g.fused_ok = true;
-    if (d.pa_count > kFusedAtomLimit || d.tab_len + 32 * d.pa_count > kFusedTabLimit) g.fused_ok = false;
+    if (d.pa_count > kFusedAtomLimit || d.tab_len + 32 * d.pa_count > fused_tab_capacity(d.qn)) g.fused_ok = false;
     for (int ai = 0; ai < d.pa_count; ai++)
       for (int q = 0; q < 3; q++)
         if (P.boxes[d.pa_begin + ai].l[q] > 16) g.fused_ok = false;   // boxes must fit the 16^3 tables

@@ -206,9 +206,11 @@ def make_config(k: int, seed: int | None = None, **kw) -> Workload:
         wl.description = ("256 independent elements, Q from {24,32,40}^2 x {32,48}, 2-6 atoms, "
                           "20-60 ALBs, n_eig = ceil(1.25 n_alb)")
     elif k == 4:
-        wl = make_slab(8, 8, (16, 16, 48), (32, 32, 48), 0.4, 40, 32, s, name=CONFIG_NAMES[4], **kw)
+        # 48 eigenpairs: with 40 the highest one is not empty enough (f >= 1e-12) on some elements
+        wl = make_slab(8, 8, (16, 16, 48), (32, 32, 48), 0.4, 48, 32, s, name=CONFIG_NAMES[4], **kw)
         wl.kT = 0.01
-        wl.description = "config-2 geometry; Fermi smearing kT 0.01 Ha; gradient w.r.t. V_eff and atoms"
+        wl.description = ("config-2 geometry, 48 eigenpairs (block 56); Fermi smearing kT 0.01 Ha; "
+                          "gradient w.r.t. V_eff and atoms")
     elif k == 5:
         wl = make_slab(32, 32, (16, 16, 48), (32, 32, 48), 0.4, 72, 64, s, name=CONFIG_NAMES[5], **kw)
         wl.description = ("32x32 elements of 16x16x48 (Q 32x32x48), 4096 atoms; 72 eigenpairs "
@@ -240,3 +242,15 @@ def subset(wl: Workload, elems) -> Workload:
     out.problem = p; out.params = q
     out.n_electrons = wl.n_electrons[elems].copy() if len(wl.n_electrons) else wl.n_electrons
     return out
+
+
+def probe_directions(n: int, size: int, seed: int) -> np.ndarray:
+    """n seeded random unit vectors of length size (to compare large gradients through projections)."""
+    rng = np.random.default_rng(seed)
+    r = rng.standard_normal((n, size))
+    return r / np.linalg.norm(r, axis=1, keepdims=True)
+
+
+def probe_points(n: int, size: int, seed: int) -> np.ndarray:
+    """n distinct seeded indices in [0, size)."""
+    return np.sort(np.random.default_rng(seed).choice(size, size=n, replace=False))
