@@ -111,13 +111,6 @@ int upload_plan(dgdft_ctx* ctx, Plan& P, cudaStream_t st) {
   g_max_points = P.max_points;
   g_max_nblk = P.max_nblk;
   g_max_nalb = P.max_nalb;
-  // radial factor tables of the fused FP32 kernel
-  P.d_gtab = (float*)ws(ctx, "p_gtab", std::max<long long>(1, P.tot_gtab) * sizeof(float));
-  if (!P.d_gtab) return fail(ctx, DGDFT_OUT_OF_MEMORY, "workspace allocation failed: p_gtab");
-  if (P.n_proj_per_atom > 0) {
-    BatchArgs b{P.d_desc, nullptr, P.M};
-    launch_build_gtab(b, P.d_fatoms, P.d_dtab32, float(P.r_cut), P.max_pa, P.d_gtab, st);
-  }
   return DGDFT_OK;
 }
 
@@ -135,7 +128,6 @@ HxArgs hx_args(const Plan& P, const int* flags, int kind, int nvec_mode) {
   a.r_cut = P.r_cut;
   a.fatoms = P.d_fatoms;
   a.dtab32 = P.d_dtab32;
-  a.gtab = P.d_gtab;
   return a;
 }
 

@@ -37,7 +37,6 @@ struct ElemDesc {
   int fmax;         // largest face (points) of E
   int face_mask;    // bit (axis*2 + side) set when that face carries DG terms
   int tab_off, tab_len;  // the element's Q-box displacement tables in dtab (contiguous)
-  long long gtab_off;    // radial factor table g of the Q boxes: [pa_count][16 z][16 y][16 x] floats
   float kscale[3];  // 1/2 (2 pi / (n_a h_a))^2 / N: kinetic multiplier per m_a^2
 };
 

@@ -102,42 +102,11 @@ struct FusedArgs {
   const int* flags;
   const FusedAtomRec* fatoms;
   const float* dtab32;
-  const float* gtab;
   const long long* xo;
   int nvec_mode;
   int npa;
   float inv_rc2;
 };
-
-// g(d) = exp(-d^2 / 2 sigma^2) (1 - d^2/rc^2)^3 inside r_cut (else 0) at every point of a Q box,
-// stored [atom][iz][iy][ix] in a 16^3 block per atom (the element's 80 vectors and all filter
-// steps share it).
-__global__ void k_build_gtab(BatchArgs b, const FusedAtomRec* fatoms, const float* dtab32, float inv_rc2,
-                             float* gtab) {
-  const int k = blockIdx.z, ai = blockIdx.y;
-  const ElemDesc& d = b.desc[k];
-  if (ai >= d.pa_count) return;
-  const FusedAtomRec& at = fatoms[d.pa_begin + ai];
-  const float* tx = dtab32 + d.tab_off + at.toff;
-  float* out = gtab + d.gtab_off + (long long)ai * 4096;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4096; i += gridDim.x * blockDim.x) {
-    const int ix = i & 15, iy = (i >> 4) & 15, iz = i >> 8;
-    float g = 0.f;
-    if (ix < at.l[0] && iy < at.l[1] && iz < at.l[2]) {
-      const float dx = tx[ix], dy = tx[at.l[0] + iy], dz = tx[at.l[0] + at.l[1] + iz];
-      const float d2 = dx * dx + dy * dy + dz * dz;
-      const float u = 1.f - d2 * inv_rc2;
-      if (u > 0.f) g = expf(-d2 * at.inv2s2) * u * u * u;
-    }
-    out[i] = g;
-  }
-}
-
-void launch_build_gtab(const BatchArgs& b, const FusedAtomRec* fatoms, const float* dtab32, float r_cut, int max_pa,
-                       float* gtab, cudaStream_t st) {
-  if (max_pa <= 0) return;
-  count_launch(); k_build_gtab<<<dim3(4, max_pa, b.M), 256, 0, st>>>(b, fatoms, dtab32, 1.f / (r_cut * r_cut), gtab);
-}
 
 constexpr int kFusedThreads = 544;   // 17 warps: y tasks (2 x 17 x 48) = 3 rounds, z tasks (2 x 17 x 32) = 2 rounds
 constexpr int kFusedWarps = kFusedThreads / 32;
@@ -599,7 +568,6 @@ int launch_fused_group(const ShapeGroup& g, const HxArgs& h, const float* X, flo
   a.flags = h.flags;
   a.fatoms = h.fatoms;
   a.dtab32 = h.dtab32;
-  a.gtab = h.gtab;
   a.xo = h.xo;
   a.nvec_mode = h.nvec_mode;
   a.npa = h.n_proj_per_atom;

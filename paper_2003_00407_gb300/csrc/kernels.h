@@ -34,7 +34,6 @@ struct HxArgs {
   double r_cut;
   const FusedAtomRec* fatoms;  // FP32 atom records (fused kernel)
   const float* dtab32;
-  const float* gtab;           // radial factor tables (fused kernel)
 };
 
 struct ShapeGroup {
@@ -97,8 +96,6 @@ void launch_gram(const BatchArgs& b, const TI* A, const long long* ao, int na_mo
                  int nb_mode, int npts_mode, const double* weight, const long long* wo, double* G, int ldg,
                  cudaStream_t st, double scale = 1.0);
 // radial factor tables g of every element's Q boxes (k_fused.cu)
-void launch_build_gtab(const BatchArgs& b, const FusedAtomRec* fatoms, const float* dtab32, float r_cut, int max_pa,
-                       float* gtab, cudaStream_t st);
 // Z_k[j][p] = sum_i W_k[i][j] X_k[i][p] (in place allowed), optional second block and residuals
 template <typename TX, typename TZ>
 void launch_rotate(const BatchArgs& b, const TX* X, const long long* xo, TZ* Z, const long long* zo, int nin_mode,

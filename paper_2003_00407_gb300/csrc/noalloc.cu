@@ -106,7 +106,6 @@ extern "C" int dgdft_apply_hamiltonian_noalloc(const dgdft_problem* prob, const 
   const size_t o_flags = b.take(P.M * sizeof(int));
   const size_t o_v64 = b.take(P.tot[OFF_V] * sizeof(double));
   const size_t o_v32 = b.take(P.tot[OFF_V] * sizeof(float));
-  const size_t o_gtab = b.take(std::max<long long>(1, P.tot_gtab) * sizeof(float));
   if (b.used > kNoAllocScratchBytes)
     return fail(nullptr, DGDFT_UNSUPPORTED,
                 "noalloc: the problem needs " + std::to_string(b.used) + " bytes of scratch, more than the fixed " +
@@ -138,16 +137,12 @@ extern "C" int dgdft_apply_hamiltonian_noalloc(const dgdft_problem* prob, const 
   const AtomBox* d_boxes = reinterpret_cast<const AtomBox*>(base + o_boxes);
   double* V64 = reinterpret_cast<double*>(base + o_v64);
   float* V32 = reinterpret_cast<float*>(base + o_v32);
-  float* gtab = reinterpret_cast<float*>(base + o_gtab);
   g_max_points = P.max_points;
   g_max_nblk = P.max_nblk;
   g_max_nalb = P.max_nalb;
   BatchArgs ba{d_desc, nullptr, P.M};
   launch_setup_v(ba, d_boxes, reinterpret_cast<const double*>(base + o_dtab), prob->v_extra, P.r_cut, V64, V32,
                  reinterpret_cast<int*>(base + o_flags), st);
-  if (P.n_proj_per_atom > 0)
-    launch_build_gtab(ba, reinterpret_cast<const FusedAtomRec*>(base + o_fat),
-                      reinterpret_cast<const float*>(base + o_dtab32), float(P.r_cut), P.max_pa, gtab, st);
   HxArgs h{};
   h.desc = d_desc;
   h.flags = nullptr;
@@ -160,7 +155,6 @@ extern "C" int dgdft_apply_hamiltonian_noalloc(const dgdft_problem* prob, const 
   h.r_cut = P.r_cut;
   h.fatoms = reinterpret_cast<const FusedAtomRec*>(base + o_fat);
   h.dtab32 = reinterpret_cast<const float*>(base + o_dtab32);
-  h.gtab = gtab;
   for (const ShapeGroup& g : P.hx.groups)
     if (!launch_fused_group(g, h, X, Y, nullptr, V32, nullptr, 0, OUT_APPLY, st))
       return fail(nullptr, DGDFT_UNSUPPORTED, "noalloc: fused kernel unavailable for a Q shape");

@@ -253,8 +253,6 @@ int build_plan(const dgdft_problem* pr, const dgdft_alb_params* prm, Plan& P, st
         d.face_mask |= 3 << (2 * a);
         d.fmax = std::max(d.fmax, d.NE / d.en[a]);
       }
-    d.gtab_off = P.tot_gtab;
-    P.tot_gtab += (long long)d.pa_count * 4096;
     d.troff = P.tot_tr;
     if (d.face_mask) P.tot_tr += 6LL * 2 * d.n_alb * d.fmax;
     P.max_points = std::max(P.max_points, d.N);

@@ -24,7 +24,6 @@ struct Plan {
   std::vector<long long> off[kOffKinds];
   long long tot[kOffKinds] = {0, 0, 0, 0, 0, 0, 0};
   long long tot_tr = 0;         // face traces
-  long long tot_gtab = 0;       // radial factor tables (floats)
   long long tot_p = 0;          // projections [n_blk][n_proj] per element
   long long tot_pe = 0;         // E-projector overlaps [n_alb][n_proj_e] per element
   long long tot_grid = 0;       // points of all domains
@@ -35,7 +34,6 @@ struct Plan {
   double* d_dtab = nullptr;
   float* d_dtab32 = nullptr;
   FusedAtomRec* d_fatoms = nullptr;
-  float* d_gtab = nullptr;
   long long* d_off[kOffKinds] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
