@@ -461,7 +461,26 @@ int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_al
     BatchArgs b{P.d_desc, c.flags, P.M};
     const long long* ox = P.d_off[OFF_X];
     launch_convert<float, double>(b, s32.B[0], ox, s64.B[0], ox, NV_BLK, st);
-    rayleigh_ritz<double>(P, c, s64, s64.B[0], st);
+    {
+      // Rayleigh-Ritz in FP64: HX64 = H X64, G1 = X64^T X64 dV, G2 = X64^T HX64 dV, W (generalised)
+      Stage<double>& s = s64;
+      const size_t mat = size_t(P.M) * P.L * P.L * sizeof(double);
+      hx<double>(P, c, c.flags, OFF_X, NV_BLK, s.B[0], s.HY, nullptr, s.S, nullptr, 0, OUT_APPLY, st);
+      CUDA_OK(cudaMemsetAsync(c.G1, 0, mat, st));
+      CUDA_OK(cudaMemsetAsync(c.G2, 0, mat, st));
+      launch_gram<double>(b, s.B[0], ox, NV_BLK, s.B[0], ox, NV_BLK, 4, nullptr, nullptr, c.G1, P.L, st);
+      launch_gram<double>(b, s.B[0], ox, NV_BLK, s.HY, ox, NV_BLK, 4, nullptr, nullptr, c.G2, P.L, st);
+      launch_rr_small(b, c.G1, c.G2, c.W, c.theta, P.L, NV_BLK, c.flags, st);
+      // residuals ||HX w - theta X w|| from FP32 copies (they sit at the FP32 floor): X32 is the FP32
+      // block itself, HX32 goes to the free FP32 unit 3; then the FP64 rotation X64 W in place
+      float* hx32 = s32.HY;
+      launch_convert<double, float>(b, s.HY, ox, hx32, ox, NV_BLK, st);
+      CUDA_OK(cudaMemsetAsync(c.resid2, 0, size_t(P.M) * P.L * sizeof(double), st));
+      launch_rotate<float, float>(b, s32.B[0], ox, nullptr, ox, NV_BLK, NV_BLK, 4, c.W, P.L, hx32, nullptr, c.theta,
+                                  c.resid2, P.L, st);
+      launch_rotate<double, double>(b, s.B[0], ox, s.B[0], ox, NV_BLK, NV_BLK, 4, c.W, P.L, nullptr, nullptr, nullptr,
+                                    nullptr, P.L, st);
+    }
     launch_final_resid(b, c.resid2, P.L, c.resid, st);
     X64 = s64.B[0];
   } else {

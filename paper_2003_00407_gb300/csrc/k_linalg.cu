@@ -130,7 +130,8 @@ void launch_gram(const BatchArgs& b, const TI* A, const long long* ao, int na_mo
 int g_max_points = 0;
 
 // ------------------------------------------------------------- rotation ----
-// Z[j][p] = sum_i W[i][j] X[i][p] over kRotTiles tiles of 16Q points per CTA; W is staged
+// Z[j][p] = sum_i W[i][j] X[i][p] over kRotTiles tiles of 16Q points per CTA (Z may be null when
+// only the residuals are wanted); W is staged
 // in shared memory once per CTA and each X tile before any Z of the same points is
 // written, so Z may alias X.  16 x 16 threads: thread (tx, ty) owns outputs
 // j = ty + 16r (r < R) at points tx + 16q (q < Q).  With X2/Z2 the same W rotates a
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(256) k_rotate(BatchArgs b, const TX* X, const 
   }
   const TX* Xk = X + xo[k];
   const TX* X2k = X2 ? X2 + xo[k] : nullptr;
-  TZ* Zk = Z + zo[k];
+  TZ* Zk = Z ? Z + zo[k] : nullptr;
   TZ* Z2k = Z2 ? Z2 + zo[k] : nullptr;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   double rsum[R];
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(256) k_rotate(BatchArgs b, const TX* X, const 
       for (int q = 0; q < Q; q++) {
         const int p = p0 + tx + 16 * q;
         if (p >= np) continue;
-        Zk[(long long)j * np + p] = TZ(acc[r][q]);
+        if (Zk) Zk[(long long)j * np + p] = TZ(acc[r][q]);
         if (Z2k) Z2k[(long long)j * np + p] = TZ(acc2[r][q]);
         if (resid2 != nullptr) {
           const double e = double(acc2[r][q]) - theta[k * ldr + j] * double(acc[r][q]);
