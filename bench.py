@@ -298,6 +298,8 @@ def run_native(args, wl, rank, world, local_rank):
                           f"of the mixed run (the DG assembly is FP64 in both paths)",
                 "alb_ms": 1000 * t64, "iterations_mean": float(np.mean(r64.iters.cpu().numpy())),
                 "mixed_vs_fp64_max_eig_diff_ha": diff}
+        # per filter pass and element: separates per-iteration speed from convergence
+        fp64["ms_per_pass_per_element"] = 1000 * t64 / max(fp64["iterations_mean"], 1e-9) / ns
 
     out = None
     if rank == 0:
@@ -312,7 +314,8 @@ def run_native(args, wl, rank, world, local_rank):
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                "clocks": clk.summary(), "fp64_gpu": fp64,
                "phase_ms": {"alb_generate": t_alb, "dg_assemble": t_dg},
-               "iterations": {"mean": float(iters.mean()), "max": int(iters.max())},
+               "iterations": {"mean": float(iters.mean()), "max": int(iters.max()),
+                              "ms_per_pass_per_element": t_alb / max(float(iters.mean()), 1e-9) / M},
                "status_nonzero": int(np.count_nonzero(status))}
     ctx.close()
     return out

@@ -267,3 +267,33 @@ def dg_assemble_host(ctx: Context, prob, params, res: ALBResult, alpha: float):
     ctx.check(ctx.lib.dgdft_dg_assemble(ctx.h, C.byref(m.prob), C.byref(m.params), C.byref(s), float(alpha),
                                         C.c_void_p(blocks.data_ptr()), _stream()))
     return blocks
+
+
+class ALBBandEnergy(torch.autograd.Function):
+    """Total Fermi-smeared band energy sum_k E_k of the local problems as a function of the global
+    V_eff correction (v_extra) and the atom positions; the backward pass returns the gradient that
+    dgdft_alb_grad forms (the local analogue of Eq. hfforce) in the same call as the forward energies.
+
+    Usage: E = ALBBandEnergy.apply(v_extra, atom_pos, ctx, prob, params, kT, n_electrons, options)
+    with v_extra [total grid points] and atom_pos [n_atoms, 3] float64 tensors and options a dict of
+    alb_generate keywords (precision, cheb_degree, tol, max_iter)."""
+
+    @staticmethod
+    def forward(fctx, v_extra, atom_pos, ctx, prob, params, kT, n_electrons, options):
+        import copy
+        dev = torch.device("cuda", ctx.device)
+        p = copy.copy(prob)
+        p.atom_pos = atom_pos.detach().to("cpu", torch.float64).numpy().copy()
+        p.v_extra = v_extra.detach().to("cpu", torch.float64).numpy().reshape(-1).copy()
+        v_dev = v_extra.detach().to(dev, torch.float64).reshape(-1).contiguous()
+        res = alb_generate(ctx, p, params, v_extra=v_dev, keep_eigvec=True, **(options or {}))
+        energy, grad_v, grad_R = alb_grad(ctx, p, params, res, kT, n_electrons)
+        fctx.save_for_backward(grad_v, grad_R)
+        fctx.shapes = (v_extra.shape, v_extra.device, atom_pos.device)
+        return energy.sum()
+
+    @staticmethod
+    def backward(fctx, g):
+        grad_v, grad_R = fctx.saved_tensors
+        vshape, vdev, rdev = fctx.shapes
+        return ((g * grad_v).reshape(vshape).to(vdev), (g * grad_R).to(rdev), None, None, None, None, None, None)
