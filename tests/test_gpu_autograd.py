@@ -47,12 +47,12 @@ def test_backward_is_the_adjoint_gradient(ctx):
     E.backward()
     res = api.alb_generate(ctx, p, q, **OPTS)
     E2, gv, gR = api.alb_grad(ctx, p, q, res, w.kT, w.n_electrons)
-    assert abs(float(E) - float(E2.sum())) <= 1e-10
+    assert abs(E.detach().item() - float(E2.sum())) <= 1e-10
     assert torch.allclose(v.grad, gv, rtol=0, atol=1e-12)
     assert torch.allclose(R.grad, gR.cpu(), rtol=0, atol=1e-12)
     sols = {k: driver.solve_element(p, q, k, dense_route=True) for k in range(p.n_elem)}
     E_o, gv_o, gR_o = driver.alb_grad(p, sols, w.kT, w.n_electrons)
-    assert abs(float(E) - E_o.sum()) <= 1e-8
+    assert abs(E.detach().item() - E_o.sum()) <= 1e-8
     assert np.abs(R.grad.numpy() - gR_o).max() <= 1e-7 * max(1.0, np.abs(gR_o).max())
     assert np.abs(v.grad.cpu().numpy() - gv_o).max() <= 1e-7 * max(1.0, np.abs(gv_o).max())
 
