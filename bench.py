@@ -351,7 +351,7 @@ def filter_roofline(ctx, api, _abi, wl, torch, stream, res):
     # DRAM bytes of one full launch: dram__bytes_read.sum + dram__bytes_write.sum of the ncu capture in
     # profiles/k_cheb_fused_16elem_full.md (16 elements), scaled by the vectors processed (x 64); only for
     # the 1024-element sheet, which that capture samples
-    traffic = 735.3e6 * (M / 16.0) if M == 1024 and int(np.max(N)) == 49152 else None
+    traffic = 738.0e6 * (M / 16.0) if M == 1024 and int(np.max(N)) == 49152 else None
     return {"bound": "hbm", "achieved": ach, "peak": peak[0], "unit": "GB/s", "frac": ach / peak[0],
             "traffic": traffic, "kernel": "k_cheb_fused (one FP32 Chebyshev step over all vectors; one launch)",
             "step_ms": 1000 * t_step, "bytes_per_step": bytes_step, "peak_source": peak[1]}

@@ -108,7 +108,9 @@ struct FusedArgs {
   float inv_rc2;
 };
 
-constexpr int kFusedThreads = 544;   // 17 warps: y tasks (2 x 17 x 48) = 3 rounds, z tasks (2 x 17 x 32) = 2 rounds
+// 28 warps (7 per scheduler, at most 72 registers a thread): more resident warps hide the shared-memory
+// and dependency latencies of the phases better than fewer warps with evenly filled rounds of line tasks
+constexpr int kFusedThreads = 896;
 constexpr int kFusedWarps = kFusedThreads / 32;
 constexpr int kFusedMaxAtoms = 96;
 constexpr int kFusedMaxTab = 3072;   // floats of displacement and x-factor tables per CTA (at most)
