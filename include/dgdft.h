@@ -56,7 +56,7 @@ enum dgdft_status {
   DGDFT_BAD_INPUT = 5,      /* NaN/Inf found in v_extra or produced by the solve */
   DGDFT_TIMEOUT = 6,        /* reserved: a bounded device wait gave up */
   DGDFT_CUDA_ERROR = 7,     /* a CUDA call failed; message in dgdft_last_error */
-  DGDFT_UNSUPPORTED = 8     /* valid but outside this build's limits (sizes, radices) */
+  DGDFT_UNSUPPORTED = 8     /* valid but outside the library's limits (sizes, radices) */
 };
 
 enum dgdft_precision {
