@@ -117,7 +117,7 @@ def query_sizes(m: Marshalled):
     out = (C.c_int64 * 6)()
     r = _abi.load().dgdft_alb_query_sizes(C.byref(m.prob), C.byref(m.params), out)
     if r != 0:
-        raise DgdftError(r, "dgdft_alb_query_sizes")
+        raise DgdftError(r, "dgdft_alb_query_sizes: " + (_abi.load().dgdft_last_error(None) or b"").decode())
     return [int(v) for v in out]
 
 

@@ -352,10 +352,11 @@ using namespace dgdft;
 extern "C" {
 
 int dgdft_alb_query_sizes(const dgdft_problem* prob, const dgdft_alb_params* params, int64_t out[6]) {
+  if (!prob || !params || !out) return fail(nullptr, DGDFT_INVALID_ARG, "null argument");
   Plan P;
   std::string msg;
   int r = build_plan(prob, params, P, msg);
-  if (r) return r;
+  if (r) return fail(nullptr, r, msg);
   out[0] = P.L;
   out[1] = P.tot[OFF_A];
   out[2] = P.tot[OFF_E];

@@ -51,6 +51,10 @@ def test_query_sizes_on_host(lib):
     (lambda p, q: p.elem_Qn.__setitem__((0, 0), 33), 1),         # Qn - En odd
     (lambda p, q: p.elem_Qn.__setitem__(slice(None), (26, 32, 48)) or p.elem_En.__setitem__(slice(None), (16, 16, 48)), 8),  # 26 = 2*13
     (lambda p, q: setattr(p, "r_cut", 30.0), 1),                 # domain side < 2 r_cut
+    (lambda p, q: q.n_blk.__setitem__(slice(None), q.n_eig - 1), 1),   # filter block smaller than n_eig
+    (lambda p, q: q.n_blk.__setitem__(slice(None), 104) or q.n_eig.__setitem__(slice(None), 100), 8),  # block > 96
+    (lambda p, q: p.dom_h.__setitem__((0, 0), 0.0), 1),          # zero grid spacing
+    (lambda p, q: p.neighbors.__setitem__((0, 1), 9999), 1),     # neighbour id out of range
 ])
 def test_query_sizes_rejects_bad_arguments(lib, mutate, code):
     import copy
@@ -63,6 +67,20 @@ def test_query_sizes_rejects_bad_arguments(lib, mutate, code):
     with pytest.raises(api.DgdftError) as e:
         api.query_sizes(m)
     assert e.value.code == code
+    assert len(str(e.value)) > len("INVALID_ARG: dgdft_alb_query_sizes: ")   # the reason is reported
+
+
+def test_query_sizes_rejects_an_empty_partition(lib):
+    from workloads import make_config
+    from workloads.configs import subset
+    from paper_2003_00407_gb300 import api
+    w = subset(make_config(2), [])
+    w.problem.n_stencil = 1
+    w.problem.neighbors = np.zeros((0, 1), dtype=np.int32)
+    m = api.Marshalled(w.problem, w.params, precision=0, cheb_degree=40, tol=1e-8, max_iter=50)
+    with pytest.raises(api.DgdftError) as e:
+        api.query_sizes(m)
+    assert e.value.code == 1
 
 
 def test_context_creation_fails_cleanly_without_gpu(lib):
