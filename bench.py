@@ -304,7 +304,7 @@ def run_native(args, wl, rank, world, local_rank):
     out = None
     if rank == 0:
         cpu = None
-        if not args.no_cpu:
+        if not args.no_cpu and world == 1:   # the oracle baseline is timed at N = 1 only
             iters_full = int(round(fp64["iterations_mean"])) if fp64 else 9
             v, desc, used = oracle_sample(wl, os.cpu_count() or 1, iters_full, args.degree)
             cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc}
