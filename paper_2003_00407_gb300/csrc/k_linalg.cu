@@ -116,7 +116,7 @@ void launch_gram(const BatchArgs& b, const TI* A, const long long* ao, int na_mo
                  int nb_mode, int npts_mode, const double* weight, const long long* wo, double* G, int ldg,
                  cudaStream_t st, double scale) {
   // callers zero G first
-  extern int g_max_points, g_max_nblk;
+
   dim3 grid((g_max_points + kGramChunk - 1) / kGramChunk, b.M);
   count_launch();
   switch (tile_r(g_max_nblk)) {
@@ -127,7 +127,7 @@ void launch_gram(const BatchArgs& b, const TI* A, const long long* ao, int na_mo
     default: k_gram<TI, 6><<<grid, 256, 0, st>>>(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, weight, wo, G, ldg, scale); break;
   }
 }
-int g_max_points = 0;
+thread_local int g_max_points = 0;
 
 // ------------------------------------------------------------- rotation ----
 // Z[j][p] = sum_i W[i][j] X[i][p] over kRotTiles tiles of 16Q points per CTA (Z may be null when
@@ -249,7 +249,7 @@ void launch_rotate(const BatchArgs& b, const TX* X, const long long* xo, TZ* Z, 
   constexpr int Q = rot_q<TX>();
   const int pts = kRotTiles * 16 * Q;
   dim3 grid((g_max_points + pts - 1) / pts, b.M);
-  extern int g_max_nblk;
+
   count_launch();
 #define DGDFT_ROT(RR)                                                                                      \
   k_rotate<TX, TZ, RR, Q><<<grid, 256, rot_smem<TX, RR>(), st>>>(b, X, xo, Z, zo, nin_mode, nout_mode, npts_mode, \

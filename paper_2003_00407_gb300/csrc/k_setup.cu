@@ -43,7 +43,7 @@ __global__ void k_setup_v(BatchArgs b, const AtomBox* boxes, const double* dtab,
 
 void launch_setup_v(const BatchArgs& b, const AtomBox* boxes, const double* dtab, const double* v_extra, double r_cut,
                     double* V64, float* V32, int* flags, cudaStream_t st) {
-  extern int g_max_points;
+
   dim3 grid((g_max_points + 255) / 256, b.M);
   count_launch(); k_setup_v<<<grid, 256, 0, st>>>(b, boxes, dtab, v_extra, r_cut, V64, V32, flags);
 }
@@ -71,12 +71,12 @@ __global__ void k_random_init(BatchArgs b, T* X, const long long* xo, unsigned l
 
 template <typename T>
 void launch_random_init(const BatchArgs& b, T* X, const long long* xo, unsigned long long seed, cudaStream_t st) {
-  extern int g_max_points;
-  extern int g_max_nblk;
+
+
   dim3 grid((g_max_points + 255) / 256, g_max_nblk, b.M);
   count_launch(); k_random_init<T><<<grid, 256, 0, st>>>(b, X, xo, seed);
 }
-int g_max_nblk = 0;
+thread_local int g_max_nblk = 0;
 
 // ---- Chebyshev filter coefficients (scaled three-term recurrence) ----
 // bounds[k] = {a0, b_low, b_up}; step 1: Y = (s1/e)(H - c)X;
@@ -118,7 +118,7 @@ __global__ void k_cheb_first(BatchArgs b, const T* X, const T* HX, T* Y, const l
 template <typename T>
 void launch_cheb_first(const BatchArgs& b, const T* X, const T* HX, T* Y, const long long* xo, const double* cheb,
                        int cheb_stride, cudaStream_t st) {
-  extern int g_max_points;
+
   dim3 grid((g_max_points + 255) / 256, g_max_nblk, b.M);
   count_launch(); k_cheb_first<T><<<grid, 256, 0, st>>>(b, X, HX, Y, xo, cheb, cheb_stride);
 }
@@ -135,7 +135,7 @@ __global__ void k_convert(BatchArgs b, const TS* X, const long long* xo, TD* Y, 
 template <typename TS, typename TD>
 void launch_convert(const BatchArgs& b, const TS* X, const long long* xo, TD* Y, const long long* yo, int nvec_mode,
                     cudaStream_t st) {
-  extern int g_max_points;
+
   dim3 grid((g_max_points + 255) / 256, nvec_mode == NV_ONE ? 1 : g_max_nblk, b.M);
   count_launch(); k_convert<TS, TD><<<grid, 256, 0, st>>>(b, X, xo, Y, yo, nvec_mode);
 }
@@ -153,7 +153,7 @@ __global__ void k_restrict(BatchArgs b, const double* X, const long long* xo, do
 }
 void launch_restrict(const BatchArgs& b, const double* X, const long long* xo, double* XE, const long long* eo,
                      int nvec_mode, cudaStream_t st) {
-  extern int g_max_points;
+
   dim3 grid((g_max_points + 255) / 256, g_max_nblk, b.M);
   count_launch(); k_restrict<<<grid, 256, 0, st>>>(b, X, xo, XE, eo, nvec_mode);
 }
@@ -196,11 +196,11 @@ __global__ void k_alb_sign(BatchArgs b, double* A, const long long* ao, double* 
   for (int i = threadIdx.x; i < d.n_eig; i += blockDim.x) Ck[i * ldc + j] = -Ck[i * ldc + j];
 }
 void launch_alb_sign(const BatchArgs& b, double* A, const long long* ao, double* C, int ldc, cudaStream_t st) {
-  extern int g_max_nalb;
+
   dim3 grid(g_max_nalb, b.M);
   count_launch(); k_alb_sign<<<grid, 256, 0, st>>>(b, A, ao, C, ldc);
 }
-int g_max_nalb = 0;
+thread_local int g_max_nalb = 0;
 
 // ---- convergence: residual norms, bounds for the next filter, active flags ----
 // resid2[k][j] holds sum_p (HX_j - theta_j X_j)^2 dV-less; resid = sqrt(resid2 dV).

@@ -141,7 +141,8 @@ void launch_elem_status(const BatchArgs& b, const int* flags, const double* resi
 template <typename T>
 void launch_scale_vec_old(const BatchArgs& b, T* v, const T* f, T* vold, const long long* o, const double* nrm2,
                           cudaStream_t st);
-extern int g_max_points, g_max_nblk, g_max_nalb;
+// per-call sizes of the current plan (set by the entry point on the calling host thread)
+extern thread_local int g_max_points, g_max_nblk, g_max_nalb;
 void launch_lanczos_bound(const BatchArgs& b, const double* alphas, const double* betas, int steps,
                           const double* fnorm2, double* bounds, double* lanczos_min, cudaStream_t st);
 void launch_first_a0(const BatchArgs& b, const double* lanczos_min, double* bounds, cudaStream_t st);
