@@ -141,6 +141,10 @@ typedef struct {
  * out[4] = total points of all domains (grad_v), out[5] = n_stencil*M*L*L (blocks). */
 int dgdft_alb_query_sizes(const dgdft_problem* prob, const dgdft_alb_params* params, int64_t out[6]);
 
+/* Creates a context on CUDA device `device` (uploads the transform twiddle tables, sets the kernels'
+ * shared-memory limits).  *ctx receives the handle, or NULL on failure: DGDFT_CUDA_ERROR when the device
+ * is missing or unusable (message from dgdft_last_error(NULL)).  dgdft_ctx_destroy frees every device
+ * and pinned buffer the context grew; NULL is ignored. */
 int dgdft_ctx_create(dgdft_ctx** ctx, int device);
 void dgdft_ctx_destroy(dgdft_ctx* ctx);
 /* Message of the last failure on ctx; with ctx == NULL, of the last failure on
@@ -151,7 +155,15 @@ const char* dgdft_last_error(const dgdft_ctx* ctx);
  * (all contexts, all threads).  For accounting in benchmarks. */
 int64_t dgdft_kernel_launches(void);
 
-/* ALB generation for all elements in one batched solve. */
+/* ALB generation for all elements in one batched solve: the lowest n_eig eigenpairs of each local
+ * Hamiltonian (Eq. LocalKS) by Chebyshev-filtered subspace iteration (Alg. CheFSI: Lanczos upper bound,
+ * scaled Chebyshev filter, Cholesky-QR, Rayleigh-Ritz; in DGDFT_MIXED an FP32 stage, then one FP64
+ * Rayleigh-Ritz sweep), their restriction to E_k and the SVD truncation to n_alb ALBs (Sec. II.A.1).
+ * result arrays are caller-allocated with the sizes of dgdft_alb_query_sizes; eigvec may be NULL (the
+ * eigenvectors then stay in the context for dgdft_dg_assemble / dgdft_alb_grad).  Returns DGDFT_OK, or
+ * DGDFT_NOT_CONVERGED / DGDFT_CHOLESKY_FAIL / DGDFT_BAD_INPUT with every element's own status in
+ * result->status and all outputs filled; DGDFT_INVALID_ARG / DGDFT_UNSUPPORTED before any GPU work;
+ * DGDFT_OUT_OF_MEMORY / DGDFT_CUDA_ERROR. */
 int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* params,
                        dgdft_alb_result* result, dgdft_stream stream);
 
