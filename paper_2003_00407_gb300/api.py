@@ -157,14 +157,16 @@ def alb_generate(ctx: Context, prob, params, *, precision=_abi.FP64, cheb_degree
                  tol_mixed=0.0, keep_eigvec=True, v_extra=None, allow_not_converged=True, host_buffers=False):
     """ALB generation for every element (dgdft_alb_generate).  Returns ALBResult of device tensors."""
     dev = torch.device("cuda", ctx.device)
-    if v_extra is None and not host_buffers:
-        v_extra = v_extra_tensor(prob, dev)
+    if v_extra is None:
+        # device tensor, or (host buffers) a pinned host copy that the library stages itself
+        v_extra = v_extra_tensor(prob, "cpu").pin_memory() if host_buffers else v_extra_tensor(prob, dev)
     m = Marshalled(prob, params, precision=precision,
                    cheb_degree=params.cheb_degree if cheb_degree is None else cheb_degree,
                    tol=params.tol if tol is None else tol,
                    max_iter=params.max_iter if max_iter is None else max_iter, tol_mixed=tol_mixed,
                    flags=_abi.HOST_BUFFERS if host_buffers else 0,
                    v_extra=None if v_extra is None else v_extra.data_ptr())
+    m.keep.append(v_extra)
     L, n_alb_tot, n_vec_tot, ncoef, _, _ = query_sizes(m)
     M = prob.n_elem
     kw = dict(dtype=torch.float64, device="cpu" if host_buffers else dev)
