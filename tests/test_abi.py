@@ -90,3 +90,32 @@ def test_context_creation_fails_cleanly_without_gpu(lib):
     h = C.c_void_p()
     assert lib.dgdft_ctx_create(C.byref(h), 0) == 7
     assert b"no CUDA device" in lib.dgdft_last_error(None)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the three C structs have the header's sizes and field offsets (compiled
+    with the host C compiler)."""
+    import shutil
+    import subprocess
+    from paper_2003_00407_gb300 import _abi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = {"dgdft_problem": _abi.Problem, "dgdft_alb_params": _abi.AlbParams, "dgdft_alb_result": _abi.AlbResult}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dgdft.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c99", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
