@@ -17,6 +17,8 @@ It is a plain, slow, obviously correct NumPy/SciPy restatement of the method
   DGHamiltonian) and the dense assembled matrix (Eq. DGEigenvalue).
 * ``grad``           -- Fermi-smeared band energy and its Hellmann-Feynman
   gradient (the local analogue of Eq. hfforce).
+* ``dg_solve``       -- eigenpairs of the assembled DG Hamiltonian (Eq.
+  DGEigenvalue) by CheFSI applied block by block (the next step of the method).
 * ``driver``         -- all of the above over every element of a workload.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
@@ -24,4 +26,4 @@ brute force and finite differences.  Parity unpinned: the Chebyshev filter's
 bound heuristics (Lanczos step count, lower bound from the largest Ritz
 value) only change iteration counts, not the converged result.
 """
-from . import local_operator, chefsi, alb, dg, grad, driver  # noqa: F401
+from . import local_operator, chefsi, alb, dg, grad, driver, dg_solve  # noqa: F401
