@@ -18,7 +18,8 @@ It is a plain, slow, obviously correct NumPy/SciPy restatement of the method
 * ``grad``           -- Fermi-smeared band energy and its Hellmann-Feynman
   gradient (the local analogue of Eq. hfforce).
 * ``dg_solve``       -- eigenpairs of the assembled DG Hamiltonian (Eq.
-  DGEigenvalue) by CheFSI applied block by block (the next step of the method).
+  DGEigenvalue) by CheFSI applied block by block, and the DG electron density
+  (the next steps of the method).
 * ``driver``         -- all of the above over every element of a workload.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,

@@ -46,3 +46,22 @@ def dg_eigenpairs(prob, blocks, n_alb, n_states, n_blk, degree, tol, max_iter, s
     op = DGOperator(prob, blocks, n_alb)
     X0 = cf.random_block(seed, 0, n_blk, op.N)
     return cf.chefsi(op, n_states, n_blk, degree, tol, max_iter, X0)
+
+
+def dg_density(prob, sols, n_alb, eps, C, n_electrons, kT):
+    """Electron density of the DG solution (Sec. II.A: rho = sum_i 2 f_i |psi_i|^2 with
+    psi_i = sum_{k,a} c_{i,ka} phi_{k,a}, each ALB phi_{k,a} supported on E_k).
+
+    eps [n] and C [n, N_b] (rows orthonormal) are DG eigenpairs; f_i is Fermi-Dirac at kT with mu fixed by
+    sum_i 2 f_i = n_electrons.  Returns (rho per element [M] arrays on E_k, mu, band energy sum 2 f eps)."""
+    from .grad import fermi, fermi_level
+    eps = np.asarray(eps, dtype=np.float64)
+    mu = fermi_level(eps, float(n_electrons), kT)
+    f = fermi(eps, mu, kT)
+    off = np.concatenate([[0], np.cumsum(np.asarray(n_alb, dtype=np.int64))])
+    rho = []
+    for k in range(prob.n_elem):
+        A = sols[k]["A"]                                  # [n_alb_k, N_E] on E_k
+        psi = C[:, off[k]:off[k + 1]] @ A                 # [n, N_E]
+        rho.append((2.0 * f[:, None] * psi * psi).sum(axis=0))
+    return rho, mu, float((2.0 * f * eps).sum())

@@ -35,3 +35,23 @@ def test_chefsi_on_hdg_matches_dense_eigensolve():
     H = dg.dense(p, blocks, n_alb)
     R = X @ H.T - r["theta"][:6, None] * X
     assert np.sqrt((R * R).sum(axis=1)).max() <= 1e-10
+
+
+def test_density_integrates_to_the_electron_count_and_matches_the_density_matrix():
+    w, blocks = _case()
+    p, n_alb = w.problem, w.params.n_alb
+    sols = _sols_dense(w)
+    H = dg.dense(p, blocks, n_alb)
+    eps, V = np.linalg.eigh(H)
+    C = V[:, :10].T
+    n_el, kT = 6.0, 0.05
+    rho, mu, e_band = dg_solve.dg_density(p, sols, n_alb, eps[:10], C, n_el, kT)
+    dV = sols[0]["dV"]
+    # the ALBs are dV-orthonormal on each E_k and the rows of C orthonormal: integral = sum 2 f = N_e
+    assert abs(sum(r.sum() for r in rho) * dV - n_el) <= 1e-9
+    assert all(np.all(r >= -1e-14) for r in rho)
+    # band energy = tr(H D) with the DG density matrix D = sum_i 2 f_i c_i c_i^T
+    from oracle.grad import fermi
+    f = fermi(eps[:10], mu, kT)
+    D = (C.T * (2.0 * f)) @ C
+    assert abs(e_band - np.trace(H @ D)) <= 1e-10 * max(1.0, abs(e_band))
