@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--degree", type=int, default=80)
     ap.add_argument("--max-iter", type=int, default=60)
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--fp64-elements", type=int, default=16, help="elements in the FP64 GPU sample (0 = skip)")
+    ap.add_argument("--fp64-elements", type=int, default=128, help="elements in the FP64 GPU sample (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--elements", type=int, default=0, help="use only the first n elements (smoke runs)")
@@ -104,72 +104,96 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------- oracle arm --
-def _oracle_sample(args_tuple):
-    """Time the oracle's own steps on one element: one H application on the filter block and one
-    CholQR2 + Rayleigh-Ritz (the per-iteration work besides the filter)."""
-    from oracle import local_operator as lo, chefsi as cf
-    prob, params, k = args_tuple
+def _oracle_solve(args_tuple):
+    """One element solved by the oracle as it stands, from its seeded random start to convergence
+    (Alg. CheFSI at the bench's degree and tolerance, then the ALB truncation); returns
+    (seconds, filter passes, converged)."""
+    from oracle import driver
+    prob, params, k, degree, tol, max_iter = args_tuple
+    params.cheb_degree = degree
     t0 = time.perf_counter()
-    op = lo.LocalOperator(prob, k)
-    X = cf.random_block(params.seed, k, int(params.n_blk[k]), op.N)
-    t_setup = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    Y = op.apply(X)
-    t_h = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    Q = cf.cholqr2(Y, op.dV)
-    cf.rayleigh_ritz(op, Q)
-    t_sub = time.perf_counter() - t0
-    return t_setup, t_h, t_sub
+    r = driver.solve_element(prob, params, k, tol=tol, max_iter=max_iter)
+    return time.perf_counter() - t0, int(r["iters"]), bool(r["converged"])
 
 
-def oracle_sample(wl, cores, iters_full, degree):
-    """Oracle elements/s on the host cores, from timed oracle steps scaled to a full solve.
+class OracleSolves:
+    """The oracle timed on the host cores: `n_elem` sheet elements solved to convergence by a spawn pool
+    of `procs` single-threaded processes (one BLAS/FFT thread each), parallel over elements.  Started
+    with start(), collected with result(); value = elements solved / wall time of the pool."""
 
-    Each of `cores` processes (one BLAS/FFT thread each) times, on its own element, one H
-    application on the filter block (t_h) and one CholQR2 + Rayleigh-Ritz (t_sub, which contains
-    one more H application).  A full solve is estimated as set-up + Lanczos (10 single-vector H
-    applications) + start-up CholQR2/RR + iters_full x ((degree - 1) t_h + t_sub) + ALB truncation
-    (neglected)."""
-    import multiprocessing as mp
-    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[v] = "1"     # inherited by the spawned workers
-    elems = list(range(min(cores, wl.problem.n_elem)))
-    ctx = mp.get_context("spawn")
-    t0 = time.perf_counter()
-    with ctx.Pool(len(elems)) as pool:
-        out = pool.map(_oracle_sample, [(wl.problem, wl.params, k) for k in elems])
-    wall = time.perf_counter() - t0
-    t_setup = statistics.mean(o[0] for o in out)
-    t_h = statistics.mean(o[1] for o in out)
-    t_sub = statistics.mean(o[2] for o in out)
-    nb = float(wl.params.n_blk[0])
-    t_full = t_setup + 10 * t_h / nb + t_sub + iters_full * ((degree - 1) * t_h + t_sub)
-    value = len(elems) / t_full
-    desc = (f"{len(elems)} elements in parallel (one process per core, 1 BLAS/FFT thread): oracle H x on the "
-            f"{int(nb)}-vector block {t_h:.2f} s, CholQR2 + Rayleigh-Ritz {t_sub:.2f} s, set-up {t_setup:.2f} s; "
-            f"full solve estimated as set-up + Lanczos + {iters_full} x ({degree - 1} H x + CholQR2/RR) = "
-            f"{t_full:.0f} s per element per core; sample wall {wall:.1f} s")
-    return value, desc, len(elems)
+    def __init__(self, wl, procs, n_elem, degree, tol, max_iter):
+        self.wl, self.procs, self.degree, self.tol, self.max_iter = wl, procs, degree, tol, max_iter
+        self.elems = list(range(min(n_elem, wl.problem.n_elem)))
+        self.pool = self.async_res = None
+
+    def start(self):
+        import multiprocessing as mp
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"     # inherited by the spawned workers
+        self.pool = mp.get_context("spawn").Pool(self.procs)
+        self.t0 = time.perf_counter()
+        jobs = [(self.wl.problem, self.wl.params, k, self.degree, self.tol, self.max_iter) for k in self.elems]
+        self.async_res = self.pool.map_async(_oracle_solve, jobs, chunksize=1)
+        return self
+
+    def result(self, timeout=3600):
+        out = self.async_res.get(timeout=timeout)
+        wall = time.perf_counter() - self.t0
+        self.pool.close()
+        self.pool.join()
+        secs = [o[0] for o in out]
+        iters = [o[1] for o in out]
+        n_conv = sum(o[2] for o in out)
+        value = len(out) / wall
+        desc = (f"{len(out)} sheet elements (32x32x48, 80-vector block, 72 eigenpairs, 64 ALBs) solved to "
+                f"convergence (degree {self.degree}, residual {self.tol:g}) by the oracle as it stands on "
+                f"{self.procs} processes (one BLAS/FFT thread each): wall {wall:.1f} s, "
+                f"{statistics.mean(secs):.1f} s per element (min {min(secs):.1f}, max {max(secs):.1f}), "
+                f"filter passes mean {statistics.mean(iters):.2f} (min {min(iters)}, max {max(iters)}), "
+                f"{n_conv}/{len(out)} converged")
+        return {"value": value, "unit": UNIT, "cores": self.procs, "kind": "oracle", "sample": desc,
+                "wall_s": wall, "elements": len(out), "iterations_mean": statistics.mean(iters)}
 
 
 def run_reference(args, wl):
+    """Reference arm: the oracle on the host cores.  A warm-up step builds one element's operator per
+    process; the timed sample solves max(steps, cores) elements to convergence on `cores` processes, and a
+    step is 1/steps of that sample (ms_per_step * steps = the sample's wall time)."""
+    import multiprocessing as mp
     cores = os.cpu_count() or 1
-    iters_full = 9   # FP64 CheFSI passes of a 32x32x48 element at degree 80 to tol 1e-8 (GPU FP64 path, same algorithm)
-    vals = []
-    desc = ""
-    for i in range(args.warmup + args.steps):
-        v, desc, used = oracle_sample(wl, cores, iters_full, args.degree)
-        if i >= args.warmup:
-            vals.append(v)
-    value = statistics.median(vals)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    if args.warmup > 0:
+        with mp.get_context("spawn").Pool(min(cores, args.warmup)) as pool:
+            pool.map(_oracle_setup, [(wl.problem, k) for k in range(min(cores, args.warmup))])
+    run = OracleSolves(wl, cores, max(args.steps, cores), args.degree, args.tol, args.max_iter).start()
+    cpu = run.result()
+    value = cpu["value"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wl.problem.n_elem / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * cpu["wall_s"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(args, wl),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _oracle_setup(args_tuple):
+    from oracle import local_operator as lo
+    prob, k = args_tuple
+    lo.LocalOperator(prob, k)
+    return k
+
+
+def fp64_sample(wl, ns):
+    """The first ns elements of the workload with their stencil kept inside the sample (neighbours outside
+    it become -1, so their off-diagonal blocks are skipped but every face term is still formed)."""
+    from workloads.configs import subset
+    ws = subset(wl, range(ns))
+    nb = ws.problem.neighbors.copy()
+    nb[nb >= ns] = -1
+    ws.problem.neighbors = nb
+    return ws
 
 
 def config_dict(args, wl):
@@ -225,8 +249,16 @@ def run_native(args, wl, rank, world, local_rank):
                                                                                               wl.alpha)
         return res, blocks
 
+    # the oracle baseline runs on the host cores (one left for this process) during the warm-up steps
+    oracle_run = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = os.cpu_count() or 1
+        procs = max(1, cores - 1)
+        oracle_run = OracleSolves(wl, procs, 2 * procs, args.degree, args.tol, args.max_iter).start()
+
     for _ in range(args.warmup):
         res, blocks = step()
+    cpu = oracle_run.result() if oracle_run is not None else None
 
     # ---- timed region ----
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[0] or 0) \
@@ -260,54 +292,51 @@ def run_native(args, wl, rank, world, local_rank):
     # ---- end to end through the C-ABI with host buffers ----
     e2e = None
     if not args.no_e2e:
+        n_e2e = max(1, min(args.steps, 2))   # the end-to-end number needs a couple of steps, not all K
         barrier()
         t0 = time.perf_counter()
-        for _ in range(max(1, args.steps)):
+        for _ in range(n_e2e):
             resh, blocksh = step(host=True)
         barrier()
-        t_e2e = (time.perf_counter() - t0) / max(1, args.steps)
+        t_e2e = (time.perf_counter() - t0) / n_e2e
         L = resh.L
         n_alb_pts = int(np.sum(q.n_alb * np.prod(p.elem_En, axis=1)))
         h2d = 8 * p.v_extra.size * 2 + 8 * M * L * L
         d2h = 8 * (3 * M * L + M * L * L + n_alb_pts) + 8 * M + 8 * M * p.n_stencil * L * L
         e2e = {"value": world * M / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    # ---- FP64 GPU path on a sample of elements ----
+    # ---- FP64 GPU path on a sample of elements (its own ALB generation and DG assembly) ----
     fp64 = None
     if args.fp64_elements > 0:
-        from workloads.configs import subset
-        ns = min(args.fp64_elements, M)
-        ws = subset(wl, range(ns))
-        ws.problem.n_stencil = 1
-        ws.problem.neighbors = np.arange(ns, dtype=np.int32)[:, None].copy()
+        ws = fp64_sample(wl, min(args.fp64_elements, M))
+        ns = ws.problem.n_elem
         barrier()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0, f1, f2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         f0.record(stream)
         r64 = api.alb_generate(ctx, ws.problem, ws.params, precision=_abi.FP64, cheb_degree=args.degree,
                                tol=args.tol, max_iter=args.max_iter, keep_eigvec=False)
         f1.record(stream)
+        api.dg_assemble(ctx, ws.problem, ws.params, r64, wl.alpha)
+        f2.record(stream)
         torch.cuda.synchronize()
-        t64 = f0.elapsed_time(f1) / 1000.0
-        t_dg_elem = t_dg / 1000.0 / M
+        t64, t64dg = f0.elapsed_time(f1) / 1000.0, f1.elapsed_time(f2) / 1000.0
         ev64 = r64.eigval.cpu().numpy()
         ev32 = res.eigval.cpu().numpy()
         n_eig = int(q.n_eig[0])
         diff = float(np.abs(ev64[:ns, :n_eig] - ev32[:ns, :n_eig]).max())
-        fp64 = {"value": ns / (t64 + t_dg_elem * ns), "unit": UNIT,
-                "sample": f"first {ns} elements, FP64 ALB generation timed + DG assembly time per element "
-                          f"of the mixed run (the DG assembly is FP64 in both paths)",
-                "alb_ms": 1000 * t64, "iterations_mean": float(np.mean(r64.iters.cpu().numpy())),
+        fp64 = {"value": ns / (t64 + t64dg), "unit": UNIT,
+                "sample": f"first {ns} elements (whole rows of the sheet; neighbours outside the sample are "
+                          f"absent), FP64 ALB generation and FP64 DG assembly timed",
+                "alb_ms": 1000 * t64, "dg_ms": 1000 * t64dg,
+                "iterations_mean": float(np.mean(r64.iters.cpu().numpy())),
                 "mixed_vs_fp64_max_eig_diff_ha": diff}
         # per filter pass and element: separates per-iteration speed from convergence
         fp64["ms_per_pass_per_element"] = 1000 * t64 / max(fp64["iterations_mean"], 1e-9) / ns
 
     out = None
     if rank == 0:
-        cpu = None
-        if not args.no_cpu and world == 1:   # the oracle baseline is timed at N = 1 only
-            iters_full = int(round(fp64["iterations_mean"])) if fp64 else 9
-            v, desc, used = oracle_sample(wl, os.cpu_count() or 1, iters_full, args.degree)
-            cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc}
+        if cpu is not None:
+            cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample", "iterations_mean")}
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config_dict(args, wl),
@@ -348,9 +377,9 @@ def filter_roofline(ctx, api, _abi, wl, torch, stream, res):
     peak = measured_peak()
     ach = bytes_step / t_step / 1e9
     del X
-    # DRAM bytes of one full launch: dram__bytes_read.sum + dram__bytes_write.sum of the ncu capture in
-    # profiles/k_cheb_fused_16elem_full.md (16 elements), scaled by the vectors processed (x 64); only for
-    # the 1024-element sheet, which that capture samples
+    # DRAM bytes of one full launch: dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of the
+    # same kernel on 16 sheet elements, scaled by the vectors processed (x 64); only for the 1024-element
+    # sheet, which that capture samples
     traffic = 738.0e6 * (M / 16.0) if M == 1024 and int(np.max(N)) == 49152 else None
     return {"bound": "hbm", "achieved": ach, "peak": peak[0], "unit": "GB/s", "frac": ach / peak[0],
             "traffic": traffic, "kernel": "k_cheb_fused (one FP32 Chebyshev step over all vectors; one launch)",

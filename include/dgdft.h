@@ -13,7 +13,7 @@
  *   dgdft_alb_grad      Fermi-smeared band energy of the local problems and
  *                       its Hellmann-Feynman gradient with respect to V_eff
  *                       and the atom positions (local analogue of Eq. hfforce).
- *   dgdft_apply_hamiltonian / dgdft_chebyshev_step
+ *   dgdft_apply_hamiltonian / dgdft_chebyshev_filter
  *                       the hot operator alone (Eq. LocalKS; Alg. CheFSI step 2).
  *
  * Conventions
@@ -114,6 +114,12 @@ typedef struct {
   int precision;             /* dgdft_precision */
   uint64_t seed;             /* SplitMix64 state of the random start */
   int flags;                 /* dgdft_flags */
+  const double* x0;          /* DATA, optional warm start (NULL = random start): packed [n_eig][N] per
+                                element, the layout of dgdft_alb_result.eigvec (e.g. the eigenvectors
+                                of a previous call with a slightly different V_eff, as in the inner SCF
+                                iterations of Sec. III).  Its n_eig vectors replace the first n_eig of
+                                the start block (FP32-rounded in DGDFT_MIXED); the guard vectors keep
+                                the SplitMix64 start.  Need not be orthonormal (CholQR2 follows). */
 } dgdft_alb_params;
 
 /* Results of dgdft_alb_generate (DATA arrays; caller allocated).  Sizes in
@@ -155,6 +161,20 @@ const char* dgdft_last_error(const dgdft_ctx* ctx);
  * (all contexts, all threads).  For accounting in benchmarks. */
 int64_t dgdft_kernel_launches(void);
 
+/* The stopping test that dgdft_alb_generate applies to one element after each CheFSI pass (Alg. CheFSI:
+ * iterate until the residuals of the wanted Ritz pairs meet the tolerance), exported so that callers and
+ * tests can check the rule on a residual history without a GPU.  Host only, no device work.
+ *   max_resid  largest residual ||H x - theta x|| (dV norm) of the first n_eig Ritz pairs after this pass
+ *   tol        DGDFT_FP64 stage: leave at max_resid <= tol (a non-finite residual also ends the stage)
+ *   tol_mixed  FP32 stage (mixed != 0): leave at max_resid <= tol_mixed, or after two consecutive passes
+ *              that each cut the residual by less than 20% and end at most at 32 * 2^-24 * |b_up|
+ *              (the FP32 rounding floor of H with spectrum bound b_up); stagnation above that level
+ *              does not end the stage (the element runs on to max_iter and reports NOT_CONVERGED)
+ *   prev_resid, stall  per-element state, updated in place; start with *prev_resid = 1e300, *stall = 0
+ * Returns 1 when the element leaves the stage, 0 when it continues, -DGDFT_INVALID_ARG for null state. */
+int dgdft_stage_converged(double max_resid, double tol, double tol_mixed, int mixed, double b_up, double* prev_resid,
+                          int* stall);
+
 /* ALB generation for all elements in one batched solve: the lowest n_eig eigenpairs of each local
  * Hamiltonian (Eq. LocalKS) by Chebyshev-filtered subspace iteration (Alg. CheFSI: Lanczos upper bound,
  * scaled Chebyshev filter, Cholesky-QR, Rayleigh-Ritz; in DGDFT_MIXED an FP32 stage, then one FP64
@@ -184,7 +204,8 @@ int dgdft_alb_grad(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_pa
                    double* grad_v, double* grad_R, dgdft_stream stream);
 
 /* The hot operator: Y = H X for packed FP64 (precision DGDFT_FP64) or FP32
- * (DGDFT_MIXED) blocks of params.n_blk vectors per element (device memory). */
+ * (DGDFT_MIXED) blocks of params.n_blk vectors per element (device memory).
+ * A non-finite v_extra on some Q_k returns DGDFT_BAD_INPUT naming element k. */
 int dgdft_apply_hamiltonian(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* params,
                             const void* X, void* Y, dgdft_stream stream);
 
@@ -214,6 +235,8 @@ int dgdft_chebyshev_filter(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdf
  *     that overlap on the GPU (other streams or host threads) race on it.
  *   - X, Y and problem->v_extra are caller-owned device buffers laid out as in
  *     dgdft_apply_hamiltonian; the call synchronises `stream` before returning.
+ *   - A non-finite v_extra on some Q_k returns DGDFT_BAD_INPUT naming element k
+ *     (Y of that element is then not valid).
  *   - Errors are reported by dgdft_last_error(NULL). */
 int dgdft_apply_hamiltonian_noalloc(const dgdft_problem* prob, const dgdft_alb_params* params, const float* X,
                                     float* Y, dgdft_stream stream);

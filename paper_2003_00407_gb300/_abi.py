@@ -29,7 +29,7 @@ class Problem(C.Structure):
 class AlbParams(C.Structure):
     _fields_ = [("n_eig", PI), ("n_alb", PI), ("n_blk", PI), ("cheb_degree", C.c_int), ("tol", C.c_double),
                 ("tol_mixed", C.c_double), ("max_iter", C.c_int), ("lanczos_steps", C.c_int),
-                ("precision", C.c_int), ("seed", C.c_uint64), ("flags", C.c_int)]
+                ("precision", C.c_int), ("seed", C.c_uint64), ("flags", C.c_int), ("x0", C.c_void_p)]
 
 
 class AlbResult(C.Structure):
@@ -54,6 +54,7 @@ FUNCTIONS = {
                                           C.c_void_p, C.c_void_p]),
     "dgdft_chebyshev_filter": (C.c_int, [C.c_void_p, C.POINTER(Problem), C.POINTER(AlbParams), PD, C.c_void_p,
                                          C.c_void_p, C.c_void_p]),
+    "dgdft_stage_converged": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, PD, PI]),
     "dgdft_apply_hamiltonian_noalloc": (C.c_int, [C.POINTER(Problem), C.POINTER(AlbParams), C.c_void_p, C.c_void_p,
                                                   C.c_void_p]),
 }

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "dgdft.h"
+#include "convergence.h"
 #include "kernels.h"
 #include "plan.h"
 
@@ -70,7 +71,7 @@ int init_twiddles(dgdft_ctx* ctx) {
     }
   if (upload_twiddles(t64.data(), t32.data()) || upload_fused_twiddles(t32.data()))
     return fail(ctx, DGDFT_CUDA_ERROR, "twiddle upload failed");
-  if (set_hx_smem_limits() || set_linalg_smem_limits()) {
+  if (set_hx_smem_limits() || set_linalg_smem_limits() || set_fused_smem_limits()) {
     cudaGetLastError();
     return fail(ctx, DGDFT_CUDA_ERROR, "cudaFuncSetAttribute(max dynamic shared memory) failed");
   }
@@ -286,16 +287,22 @@ void cholqr(Plan& P, const Common& c, T* Y, double rel_shift, cudaStream_t st) {
   launch_rotate<T, T>(b, Y, ox, Y, ox, NV_BLK, NV_BLK, 4, c.W, P.L, nullptr, nullptr, nullptr, nullptr, P.L, st);
 }
 
-// One precision stage of CheFSI.  On entry B[0] holds the start block (random or
-// promoted); on exit B[0] holds the Ritz vectors of every element.
+// One precision stage of CheFSI.  On entry B[0] holds the random start block; a warm start x0
+// ([n_eig][N] per element, eigvec layout) replaces its first n_eig vectors after the Lanczos bound,
+// which keeps its random vector 0 (a Lanczos run started from an eigenvector stops at once and
+// would give no bound).  On exit B[0] holds the Ritz vectors of every element.
 template <typename T>
 int chefsi_stage(dgdft_ctx* ctx, Plan& P, const Common& c, Stage<T>& s, const dgdft_alb_params* prm, int degree,
-                 int lsteps, bool mixed, cudaStream_t st, double* history) {
+                 int lsteps, bool mixed, cudaStream_t st, double* history, const double* x0) {
   if (history)
     for (int i = 0; i < prm->max_iter + 2; i++) history[i] = -1.0;
   BatchArgs b{P.d_desc, c.flags, P.M};
   const double rel_shift = sizeof(T) == 4 ? 1e-6 : 1e-13;
   lanczos<T>(P, c, s, lsteps, st);
+  if (x0) {
+    BatchArgs ball{P.d_desc, nullptr, P.M};
+    launch_convert<double, T>(ball, x0, P.d_off[OFF_E], s.B[0], P.d_off[OFF_X], NV_EIG, st);
+  }
   cholqr<T>(P, c, s.B[0], rel_shift, st);
   cholqr<T>(P, c, s.B[0], rel_shift, st);
   rayleigh_ritz<T>(P, c, s, s.B[0], st);
@@ -405,6 +412,12 @@ const char* dgdft_last_error(const dgdft_ctx* c) { return c ? c->err.c_str() : g
 
 int64_t dgdft_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
+int dgdft_stage_converged(double max_resid, double tol, double tol_mixed, int mixed, double b_up, double* prev_resid,
+                          int* stall) {
+  if (!prev_resid || !stall) return -DGDFT_INVALID_ARG;
+  return stage_converged(max_resid, tol, tol_mixed, mixed, b_up, prev_resid, stall);
+}
+
 int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* prm,
                        dgdft_alb_result* res, dgdft_stream stream) {
   if (!ctx || !prob || !prm || !res) return fail(ctx, DGDFT_INVALID_ARG, "null argument");
@@ -431,6 +444,13 @@ int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_al
     CUDA_OK(cudaMemcpyAsync(d, vx, P.tot_grid * sizeof(double), cudaMemcpyHostToDevice, st));
     vx = d;
   }
+  const double* x0 = prm->x0;   // warm start [n_eig][N] per element (eigvec layout)
+  if (host && x0) {
+    double* d;
+    WS(d, "x0_stage", P.tot[OFF_E] * sizeof(double));
+    CUDA_OK(cudaMemcpyAsync(d, x0, P.tot[OFF_E] * sizeof(double), cudaMemcpyHostToDevice, st));
+    x0 = d;
+  }
   CUDA_OK(cudaMemsetAsync(c.flags, 0, M * sizeof(int), st));
   CUDA_OK(cudaMemsetAsync(c.iters, 0xFF, M * sizeof(int), st));   // -1: the start-up Rayleigh-Ritz is not a pass
   CUDA_OK(cudaMemsetAsync(c.stall, 0, M * sizeof(int), st));
@@ -452,7 +472,7 @@ int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_al
     const int u32[4] = {0, 1, 2, 3};
     if ((r = get_stage<float>(ctx, P, s32, 6, u32))) return r;
     launch_random_init<float>(ball, s32.B[0], P.d_off[OFF_X], prm->seed, st);
-    if ((r = chefsi_stage<float>(ctx, P, c, s32, prm, degree, lsteps, true, st, res->history))) return r;
+    if ((r = chefsi_stage<float>(ctx, P, c, s32, prm, degree, lsteps, true, st, res->history, x0))) return r;
     // final FP64 Rayleigh-Ritz sweep on the FP32 Ritz vectors: X64 in place, HX64 over B1/B2 of the FP32 stage.
     // The FP32 block is orthonormal only to FP32 accuracy; the Rayleigh-Ritz solve takes the Cholesky
     // factor of its FP64 Gram matrix (generalised problem), so no separate CholQR pass is needed.
@@ -488,7 +508,7 @@ int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_al
     const int u64[4] = {0, 2, 4, 6};
     if ((r = get_stage<double>(ctx, P, s64, 8, u64))) return r;
     launch_random_init<double>(ball, s64.B[0], P.d_off[OFF_X], prm->seed, st);
-    if ((r = chefsi_stage<double>(ctx, P, c, s64, prm, degree, lsteps, false, st, res->history))) return r;
+    if ((r = chefsi_stage<double>(ctx, P, c, s64, prm, degree, lsteps, false, st, res->history, x0))) return r;
     X64 = s64.B[0];
   }
   CUDA_OK(cudaGetLastError());
@@ -572,7 +592,12 @@ int dgdft_apply_hamiltonian(dgdft_ctx* ctx, const dgdft_problem* prob, const dgd
   else
     hx<double>(P, c, nullptr, OFF_X, NV_BLK, (const double*)X, (double*)Y, nullptr, S, nullptr, 0, OUT_APPLY, st);
   CUDA_OK(cudaGetLastError());
+  std::vector<int> hf(P.M);
+  CUDA_OK(cudaMemcpyAsync(hf.data(), c.flags, P.M * sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_OK(cudaStreamSynchronize(st));
+  for (int k = 0; k < P.M; k++)
+    if (hf[k] & EF_BAD)
+      return fail(ctx, DGDFT_BAD_INPUT, "element " + std::to_string(k) + ": v_extra is not finite on Q");
   return DGDFT_OK;
 }
 

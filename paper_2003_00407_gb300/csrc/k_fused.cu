@@ -536,17 +536,23 @@ template <int QX, int QY, int QZ>
 static int launch_shape(const ShapeGroup& g, const FusedArgs& a, const float* X, float* Y, const float* Yprev,
                         const float* V, const double* cheb, int cheb_stride, int out_mode, cudaStream_t st) {
   if (g.qn[0] != QX || g.qn[1] != QY || g.qn[2] != QZ) return 0;
-  static bool attr = false;
   constexpr int sm = fused_smem_bytes<QX, QY, QZ>();
-  if (!attr) {
-    if (allow_max_smem(k_cheb_fused<QX, QY, QZ>)) return 0;
-    attr = true;
-  }
   FusedArgs b = a;
   b.elems = g.d_elems;
   dim3 grid(g.max_nvec, g.n_elems);
   count_launch(); k_cheb_fused<QX, QY, QZ><<<grid, kFusedThreads, sm, st>>>(b, X, Yprev, Y, V, cheb, cheb_stride, out_mode);
   return 1;
+}
+
+// Shared-memory limit of every fused instance on the current device (the attribute is per device:
+// called once per device by context creation and by the allocation-free entry point's set-up).
+int set_fused_smem_limits() {
+  int e = 0;
+#define DGDFT_ATTR(a, b, c) \
+  if (!e) e = allow_max_smem(k_cheb_fused<a, b, c>);
+  DGDFT_FUSED_SHAPES(DGDFT_ATTR)
+#undef DGDFT_ATTR
+  return e;
 }
 
 // Displacement-table capacity (floats) of the fused instance for this Q shape; 0 = no instance.

@@ -3,6 +3,7 @@
 // Lanczos upper bound (step 1), convergence bookkeeping, restriction to E and
 // the display sign of the ALBs.
 #include "kernels.h"
+#include "convergence.h"
 
 namespace dgdft {
 
@@ -203,9 +204,9 @@ void launch_alb_sign(const BatchArgs& b, double* A, const long long* ao, double*
 thread_local int g_max_nalb = 0;
 
 // ---- convergence: residual norms, bounds for the next filter, active flags ----
-// resid2[k][j] holds sum_p (HX_j - theta_j X_j)^2 dV-less; resid = sqrt(resid2 dV).
-// FP32 stage (mixed=1): an element also leaves when max residual <= tol_mixed or
-// after two iterations that reduce it by less than 20% (the FP32 floor).
+// resid2[k][j] holds sum_p (HX_j - theta_j X_j)^2 dV-less; resid = sqrt(resid2 dV).  The stopping
+// test is stage_converged (convergence.h): tol, and in the FP32 stage tol_mixed or stagnation at the
+// FP32 rounding floor.
 __global__ void k_update_convergence(BatchArgs b, const double* resid2, int ldr, double* resid, const double* theta,
                                      double* bounds, double tol, double tol_mixed, int mixed, double* prev_res,
                                      int* stall, int* flags, int* active_count, int* iters) {
@@ -223,17 +224,8 @@ __global__ void k_update_convergence(BatchArgs b, const double* resid2, int ldr,
   bounds[3 * k] = theta[k * ldr];
   bounds[3 * k + 1] = theta[k * ldr + d.n_blk - 1];
   iters[k] += 1;
-  bool done = mx <= tol || !isfinite(mx);
   if (!isfinite(mx)) atomicOr(&flags[k], EF_BAD);
-  if (mixed) {
-    // FP32 stage: stop at tol_mixed, or after two iterations that reduce the residual by less
-    // than 20% (the FP32 floor; the subspace keeps improving while the residual, dominated by
-    // high-energy rounding noise, stagnates, so the second stagnating pass is kept)
-    if (mx <= tol_mixed) done = true;
-    if (mx > 0.8 * prev_res[k]) stall[k] += 1; else stall[k] = 0;
-    if (stall[k] >= 2) done = true;
-  }
-  prev_res[k] = mx;
+  const bool done = stage_converged(mx, tol, tol_mixed, mixed, bounds[3 * k + 2], &prev_res[k], &stall[k]) != 0;
   if (isfinite(mx)) atomicMax(hist_max, (unsigned long long)__double_as_longlong(mx));
   if (done) atomicAnd(&flags[k], ~EF_ACTIVE);
   else atomicAdd(active_count, 1);

@@ -52,6 +52,7 @@ struct HxPlan {
 };
 
 int fused_shape_supported(const int qn[3]);
+int set_fused_smem_limits();   // per device; returns the cudaError_t
 int fused_tab_capacity(const int qn[3]);
 // fused FP32 Chebyshev step (k_fused.cu): returns 1 when it handled the group
 int launch_fused_group(const ShapeGroup& g, const HxArgs& h, const float* X, float* Y, const float* Yprev,

@@ -60,6 +60,10 @@ static int noalloc_setup(unsigned char** out) {
       cudaGetLastError();
       return fail(nullptr, DGDFT_CUDA_ERROR, "noalloc: twiddle upload failed");
     }
+    if (set_fused_smem_limits()) {
+      cudaGetLastError();
+      return fail(nullptr, DGDFT_CUDA_ERROR, "noalloc: shared-memory limit of the fused kernel not set");
+    }
     st.ptr = static_cast<unsigned char*>(p);
     st.ready = true;
   }
@@ -161,5 +165,12 @@ extern "C" int dgdft_apply_hamiltonian_noalloc(const dgdft_problem* prob, const 
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(nullptr, DGDFT_CUDA_ERROR, std::string("noalloc: ") + cudaGetErrorString(e));
+  // non-finite v_extra on some Q (flag set by the V_eff set-up): the output of that element is not valid
+  std::vector<int> hf(P.M);
+  e = cudaMemcpy(hf.data(), base + o_flags, P.M * sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(nullptr, DGDFT_CUDA_ERROR, std::string("noalloc: ") + cudaGetErrorString(e));
+  for (int k = 0; k < P.M; k++)
+    if (hf[k] & EF_BAD)
+      return fail(nullptr, DGDFT_BAD_INPUT, "noalloc: element " + std::to_string(k) + ": v_extra is not finite on Q");
   return DGDFT_OK;
 }

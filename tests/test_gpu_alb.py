@@ -62,3 +62,22 @@ def test_small_slab_with_projectors(ctx, precision):
     res = api.alb_generate(ctx, w.problem, w.params, precision=precision, cheb_degree=12, tol=1e-9, max_iter=300)
     print("iters", res.iters.cpu().numpy())
     _check(w, res, refs, range(w.problem.n_elem))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_warm_start_from_converged_vectors(ctx, precision):
+    """x0 (the inner-SCF warm start of Sec. III): started from the eigenvectors of a converged call, the
+    same problem needs no FP64 filter pass (the start-up Rayleigh-Ritz already meets tol) and at most the
+    two stagnation passes of the FP32 stage, against several passes from the random start; the results
+    keep the parity contract."""
+    from paper_2003_00407_gb300 import api
+    w = make_slab(3, 2, (8, 6, 12), (16, 12, 12), 0.45, 10, 6, 5, r_cut=2.6, width=0.7, proj_width=0.7)
+    refs = {k: driver.solve_element(w.problem, w.params, k, dense_route=True) for k in range(w.problem.n_elem)}
+    kw = dict(precision=precision, cheb_degree=12, tol=1e-9, max_iter=300)
+    cold = api.alb_generate(ctx, w.problem, w.params, **kw)
+    warm = api.alb_generate(ctx, w.problem, w.params, x0=cold.eigvec.clone(), **kw)
+    ic, iw = cold.iters.cpu().numpy(), warm.iters.cpu().numpy()
+    print("cold passes", ic, "warm passes", iw)
+    assert ic.min() >= 3
+    assert iw.max() <= (0 if precision == 0 else 2), iw
+    _check(w, warm, refs, range(w.problem.n_elem))

@@ -66,3 +66,17 @@ def test_chebyshev_filter_matches_oracle(ctx, precision):
         o += ref.size
         err = np.abs(got - ref).max() / np.abs(ref).max()
         assert err < (1e-11 if precision == 0 else 2e-5), (k, err)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_apply_hamiltonian_reports_non_finite_v_extra(ctx, precision):
+    from paper_2003_00407_gb300 import api
+    w = CASES["slab_proj_small"]()
+    p, q = w.problem, w.params
+    p.v_extra = p.v_extra.copy()
+    p.v_extra[7] = np.nan
+    rng = np.random.default_rng(2)
+    _, flat = packed_blocks(p, q.n_blk, rng, np.float64 if precision == 0 else np.float32)
+    with pytest.raises(api.DgdftError) as e:
+        api.apply_hamiltonian(ctx, p, q, torch.as_tensor(flat, device="cuda"), precision=precision)
+    assert "BAD_INPUT" in str(e.value) and "not finite" in str(e.value)
