@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--fp64-elements", type=int, default=128, help="elements in the FP64 GPU sample (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-elements", type=int, default=0,
+                    help="elements the oracle baseline solves (0 = two per host process)")
     ap.add_argument("--elements", type=int, default=0, help="use only the first n elements (smoke runs)")
     ap.add_argument("--only-filter", action="store_true",
                     help="time only the FP32 Chebyshev filter (degree --degree) on random blocks (profiling)")
@@ -254,7 +256,8 @@ def run_native(args, wl, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = os.cpu_count() or 1
         procs = max(1, cores - 1)
-        oracle_run = OracleSolves(wl, procs, 2 * procs, args.degree, args.tol, args.max_iter).start()
+        n_cpu = args.cpu_elements if args.cpu_elements > 0 else 2 * procs
+        oracle_run = OracleSolves(wl, min(procs, n_cpu), n_cpu, args.degree, args.tol, args.max_iter).start()
 
     for _ in range(args.warmup):
         res, blocks = step()

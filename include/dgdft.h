@@ -195,6 +195,38 @@ int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_al
 int dgdft_dg_assemble(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* params,
                       const dgdft_alb_result* result, double alpha, double* blocks, dgdft_stream stream);
 
+/* The two halves of dgdft_dg_assemble, for callers that distribute the elements (Sec. II.B: the
+ * elements are split among processes, and building H^DG needs the face and projector data of the
+ * neighbouring elements, which are exchanged point to point).  An element's DG ingredients depend only
+ * on its own ALBs; the blocks of element k need the ingredients of k and of its stencil neighbours.
+ *
+ * Layout of the ingredients of a problem (DATA arrays, scalars):
+ *   kv      [M][L][L]   kinetic + V_eff part of the diagonal block (L as in dgdft_alb_query_sizes)
+ *   traces  element k's record at tr_off[k]: [6 faces][2][n_alb_k][F_k] -- face = 2*axis + (1 on the
+ *           high side), kind 0 = value, 1 = outward-axis derivative of the ALB interpolant on the face
+ *           plane half a spacing outside E_k; F_k = the element's largest face (points), a face's points
+ *           run over the two transverse axes of E_k (lower axis fastest); faces along axes the stencil
+ *           does not name, or along which E_k spans its domain, are zero; records of elements without
+ *           such faces are empty
+ *   proj    element k's record at pe_off[k]: [n_alb_k][P_k], P_k projector columns of the atoms whose
+ *           support meets E_k, in ascending atom order, n_proj_per_atom columns each
+ * dgdft_dg_query_layout (host only) fills tr_off[M+1] and pe_off[M+1] (cumulative, last entry = total).
+ * Records depend only on the element's own geometry and the atoms, so the record of an element is the
+ * same in every problem that contains it: a record computed by one process can be copied into the
+ * arrays of another process's problem at that problem's offsets.
+ *
+ * dgdft_dg_ingredients fills kv/traces/proj from a dgdft_alb_generate result (like dgdft_dg_assemble).
+ * dgdft_dg_blocks forms blocks [M][n_stencil][L][L] from ingredients; the blocks of an element are
+ * valid when its own record and those of its neighbours are filled (a neighbour id -1 gives zero
+ * blocks).  Status codes as dgdft_dg_assemble; dgdft_dg_assemble equals the two calls in a row. */
+int dgdft_dg_query_layout(const dgdft_problem* prob, const dgdft_alb_params* params, int64_t* tr_off,
+                          int64_t* pe_off);
+int dgdft_dg_ingredients(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* params,
+                         const dgdft_alb_result* result, double* kv, double* traces, double* proj,
+                         dgdft_stream stream);
+int dgdft_dg_blocks(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* params, const double* kv,
+                    const double* traces, const double* proj, double alpha, double* blocks, dgdft_stream stream);
+
 /* Band energy E_k = sum_j 2 f_j lambda_j (f Fermi-Dirac at kT, mu_k fixed by
  * n_electrons[k], a host array) and its gradient: energy DATA [M],
  * grad_v DATA [total points of all domains] (dE/dV at each grid point,

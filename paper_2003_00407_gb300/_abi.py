@@ -54,6 +54,11 @@ FUNCTIONS = {
                                           C.c_void_p, C.c_void_p]),
     "dgdft_chebyshev_filter": (C.c_int, [C.c_void_p, C.POINTER(Problem), C.POINTER(AlbParams), PD, C.c_void_p,
                                          C.c_void_p, C.c_void_p]),
+    "dgdft_dg_query_layout": (C.c_int, [C.POINTER(Problem), C.POINTER(AlbParams), PL, PL]),
+    "dgdft_dg_ingredients": (C.c_int, [C.c_void_p, C.POINTER(Problem), C.POINTER(AlbParams), C.POINTER(AlbResult),
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dgdft_dg_blocks": (C.c_int, [C.c_void_p, C.POINTER(Problem), C.POINTER(AlbParams), C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     "dgdft_stage_converged": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, PD, PI]),
     "dgdft_apply_hamiltonian_noalloc": (C.c_int, [C.POINTER(Problem), C.POINTER(AlbParams), C.c_void_p, C.c_void_p,
                                                   C.c_void_p]),

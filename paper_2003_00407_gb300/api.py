@@ -309,3 +309,75 @@ class ALBBandEnergy(torch.autograd.Function):
         grad_v, grad_R = fctx.saved_tensors
         vshape, vdev, rdev = fctx.shapes
         return ((g * grad_v).reshape(vshape).to(vdev), (g * grad_R).to(rdev), None, None, None, None, None, None)
+
+
+def dg_layout(prob, params):
+    """(tr_off [M+1], pe_off [M+1]) int64: offsets of the per-element DG ingredient records
+    (dgdft_dg_query_layout, host only)."""
+    m = Marshalled(prob, params, precision=_abi.FP64, cheb_degree=max(2, params.cheb_degree), tol=params.tol,
+                   max_iter=params.max_iter)
+    M = prob.n_elem
+    tr = np.zeros(M + 1, dtype=np.int64)
+    pe = np.zeros(M + 1, dtype=np.int64)
+    lib = _abi.load()
+    r = lib.dgdft_dg_query_layout(C.byref(m.prob), C.byref(m.params), _ptr(tr, C.c_int64), _ptr(pe, C.c_int64))
+    if r != 0:
+        raise DgdftError(r, "dgdft_dg_query_layout: " + (lib.dgdft_last_error(None) or b"").decode())
+    return tr, pe
+
+
+def dg_ingredients(ctx: Context, prob, params, res: ALBResult):
+    """(kv [M, L, L], traces [tr_off[M]], proj [pe_off[M]]) device tensors (dgdft_dg_ingredients)."""
+    m, s = res.struct
+    dev = torch.device("cuda", ctx.device)
+    v = v_extra_tensor(prob, dev)
+    m.keep.append(v)
+    m.prob.v_extra = C.c_void_p(v.data_ptr())
+    tr, pe = dg_layout(prob, params)
+    M, L = prob.n_elem, res.L
+    kv = torch.empty(M, L, L, dtype=torch.float64, device=dev)
+    traces = torch.zeros(max(1, int(tr[-1])), dtype=torch.float64, device=dev)
+    proj = torch.zeros(max(1, int(pe[-1])), dtype=torch.float64, device=dev)
+    ctx.check(ctx.lib.dgdft_dg_ingredients(ctx.h, C.byref(m.prob), C.byref(m.params), C.byref(s),
+                                           C.c_void_p(kv.data_ptr()), C.c_void_p(traces.data_ptr()),
+                                           C.c_void_p(proj.data_ptr()), _stream()))
+    return kv, traces, proj
+
+
+def dg_blocks(ctx: Context, prob, params, kv, traces, proj, alpha: float):
+    """DG blocks [M, n_stencil, L, L] from ingredient arrays (dgdft_dg_blocks); L = kv.shape[1]."""
+    dev = torch.device("cuda", ctx.device)
+    m = Marshalled(prob, params, precision=_abi.FP64, cheb_degree=max(2, params.cheb_degree), tol=params.tol,
+                   max_iter=params.max_iter)
+    M, L = prob.n_elem, int(kv.shape[1])
+    blocks = torch.empty(M, int(prob.n_stencil), L, L, dtype=torch.float64, device=dev)
+    ctx.check(ctx.lib.dgdft_dg_blocks(ctx.h, C.byref(m.prob), C.byref(m.params), C.c_void_p(kv.data_ptr()),
+                                      C.c_void_p(traces.data_ptr()), C.c_void_p(proj.data_ptr()), float(alpha),
+                                      C.c_void_p(blocks.data_ptr()), _stream()))
+    return blocks
+
+
+def result_subset(res: ALBResult, prob, params, elems, sub_prob, sub_params, precision=_abi.FP64):
+    """The part of an alb_generate result that belongs to `elems` (in that order), as a result of the
+    sub-problem (sub_prob, sub_params) over those elements: per-element rows and packed records are
+    copied (device tensors); the eigenvectors must have been kept."""
+    if res.eigvec is None:
+        raise ValueError("result_subset needs the eigenvectors (alb_generate(keep_eigvec=True))")
+    elems = np.asarray(elems, dtype=np.int64)
+    NE = np.prod(prob.elem_En, axis=1).astype(np.int64)
+    N = np.prod(prob.elem_Qn, axis=1).astype(np.int64)
+    a_off = np.concatenate([[0], np.cumsum(params.n_alb.astype(np.int64) * NE)])
+    e_off = np.concatenate([[0], np.cumsum(params.n_eig.astype(np.int64) * N)])
+    idx = torch.as_tensor(elems, device=res.eigval.device)
+    m = Marshalled(sub_prob, sub_params, precision=precision, cheb_degree=max(2, sub_params.cheb_degree),
+                   tol=sub_params.tol, max_iter=sub_params.max_iter)
+    L = query_sizes(m)[0]
+    if L != res.L:
+        raise ValueError("the sub-problem's row length differs from the result's")
+    cat = lambda t, off: torch.cat([t[int(off[k]):int(off[k + 1])] for k in elems]) if len(elems) else t[:0]
+    sub = ALBResult(eigval=res.eigval[idx].contiguous(), resid=res.resid[idx].contiguous(),
+                    sing=res.sing[idx].contiguous(), coef=res.coef[idx].contiguous(),
+                    alb=cat(res.alb, a_off).contiguous(), eigvec=cat(res.eigvec, e_off).contiguous(),
+                    iters=res.iters[idx].contiguous(), status=res.status[idx].contiguous(), L=L, code=res.code)
+    sub.struct = (m, sub.as_struct())
+    return sub

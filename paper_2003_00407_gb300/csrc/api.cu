@@ -651,6 +651,187 @@ int dgdft_chebyshev_filter(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdf
   return DGDFT_OK;
 }
 
+}  // extern "C"
+
+namespace dgdft {
+
+// Element-local DG ingredients (Eq. DGHamiltonian): KV = kinetic + V_eff part of the diagonal block
+// [M][L][L], face traces TR (packed per element at desc.troff) and projector overlaps on E, PE (packed
+// at desc.peoff).  Every pointer is a device pointer.
+static int dg_ingredients_dev(dgdft_ctx* ctx, Plan& P, const Common& c, const double* eigvec, const double* coef,
+                              const double* vx, double* KV, double* TR, double* PE, cudaStream_t st) {
+  const size_t M = P.M, L = P.L;
+  BatchArgs b{P.d_desc, nullptr, P.M};
+  CUDA_OK(cudaMemsetAsync(c.flags, 0, M * sizeof(int), st));
+  launch_setup_v(b, P.d_boxes, P.d_dtab, vx, P.r_cut, c.V64, c.V32, c.flags, st);
+  // psi^Q = C^T Phi^Q (trig interpolant of the ALBs on Q), its restriction A to E
+  double *Psi, *D, *PsiE, *VE;
+  cplx<double>* S;
+  {
+    char* ar = arena(ctx, P, 4);
+    if (!ar) return fail(ctx, DGDFT_OUT_OF_MEMORY, "out of device memory: block arena");
+    Psi = (double*)ar;
+    D = (double*)(ar + 2 * size_t(P.tot[OFF_X]) * 4);
+  }
+  WS(PsiE, "PhiE", P.tot[OFF_FE] * sizeof(double));
+  WS(VE, "dg_ve", P.tot[OFF_VE] * sizeof(double));
+  WS(S, "S_spec", size_t(P.tot[OFF_S]) * sizeof(cplx<double>));
+  const long long* oe = P.d_off[OFF_E];
+  const long long* ofe = P.d_off[OFF_FE];
+  launch_rotate<double, double>(b, eigvec, oe, Psi, oe, NV_EIG, NV_ALB, 4, coef, P.L, nullptr, nullptr, nullptr,
+                                nullptr, P.L, st);
+  // kinetic: 1/2 sum_axes (d psi)_E^T (d psi)_E dV with spectral derivatives (Nyquist dropped)
+  CUDA_OK(cudaMemsetAsync(KV, 0, M * L * L * sizeof(double), st));
+  set_group_nvec(P, NV_ALB);
+  HxArgs ha = hx_args(P, nullptr, OFF_E, NV_ALB);
+  for (int axis = 0; axis < 3; axis++) {
+    launch_forward<double>(P.hx, ha, Psi, S, st);
+    launch_zline<double>(P.hx, ha, S, MULT_DX + axis, st);
+    launch_inverse_raw<double>(P.hx, ha, S, D, st);
+    launch_restrict(b, D, oe, PsiE, ofe, NV_ALB, st);
+    launch_gram<double>(b, PsiE, ofe, NV_ALB, PsiE, ofe, NV_ALB, 5, nullptr, nullptr, KV, P.L, st, 0.5);
+  }
+  // V_eff term: A diag(V_E) A^T dV with A = psi restricted to E
+  launch_restrict(b, c.V64, P.d_off[OFF_V], VE, P.d_off[OFF_VE], NV_ONE, st);
+  launch_restrict(b, Psi, oe, PsiE, ofe, NV_ALB, st);
+  launch_gram<double>(b, PsiE, ofe, NV_ALB, PsiE, ofe, NV_ALB, 5, VE, P.d_off[OFF_VE], KV, P.L, st);
+  // projector overlaps on E and face traces
+  if (P.tot_pe > 0) CUDA_OK(cudaMemsetAsync(PE, 0, P.tot_pe * sizeof(double), st));
+  launch_proj_overlap(b, P.d_boxes, P.d_dtab, PsiE, ofe, P.r_cut, P.n_proj_per_atom, PE, P.max_pe, st);
+  if (P.tot_tr > 0) {
+    CUDA_OK(cudaMemsetAsync(TR, 0, P.tot_tr * sizeof(double), st));
+    launch_face_traces(b, Psi, oe, TR, st);
+  }
+  CUDA_OK(cudaGetLastError());
+  return DGDFT_OK;
+}
+
+// Blocks from the ingredients (device pointers): the stencil of every element of the plan.
+static int dg_blocks_dev(dgdft_ctx* ctx, Plan& P, const dgdft_problem* prob, const double* KV, const double* TR,
+                         const double* PE, double alpha, double* out, cudaStream_t st) {
+  const size_t M = P.M;
+  int* d_nb;
+  WS(d_nb, "dg_nb", std::max<size_t>(1, M * P.n_stencil) * sizeof(int));
+  {
+    std::vector<int> nb(M * P.n_stencil);
+    for (size_t k = 0; k < M; k++)
+      for (int s = 0; s < P.n_stencil; s++)
+        nb[k * P.n_stencil + s] = P.n_stencil > 1 ? prob->neighbors[k * P.n_stencil + s] : int(k);
+    CUDA_OK(cudaMemcpyAsync(d_nb, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
+  BatchArgs b{P.d_desc, nullptr, P.M};
+  launch_dg_blocks(b, d_nb, P.n_stencil, TR, PE, P.d_boxes, P.n_proj_per_atom, KV, P.L, alpha, out, st);
+  CUDA_OK(cudaGetLastError());
+  return DGDFT_OK;
+}
+
+static int dg_eigvec(dgdft_ctx* ctx, const Plan& P, const dgdft_alb_result* res, bool host, const double** out) {
+  const double* eigvec = (host || res->eigvec == nullptr) ? nullptr : res->eigvec;
+  if (!eigvec) {
+    auto it = ctx->bufs.find("eigvec_ws");
+    if (it == ctx->bufs.end() || it->second.second < size_t(P.tot[OFF_E]) * sizeof(double))
+      return fail(ctx, DGDFT_INVALID_ARG, "no eigenvectors: pass result->eigvec or call dgdft_alb_generate first");
+    eigvec = (const double*)it->second.first;
+  }
+  *out = eigvec;
+  return DGDFT_OK;
+}
+
+// Stages a host array into a named workspace buffer (host == true) or returns the device pointer as is.
+static int stage_in(dgdft_ctx* ctx, bool host, const char* name, const double* src, size_t n, const double** out,
+                    cudaStream_t st) {
+  if (!host || src == nullptr) {
+    *out = src;
+    return DGDFT_OK;
+  }
+  double* d;
+  WS(d, name, std::max<size_t>(1, n) * sizeof(double));
+  if (n) CUDA_OK(cudaMemcpyAsync(d, src, n * sizeof(double), cudaMemcpyHostToDevice, st));
+  *out = d;
+  return DGDFT_OK;
+}
+
+}  // namespace dgdft
+
+extern "C" {
+
+int dgdft_dg_query_layout(const dgdft_problem* prob, const dgdft_alb_params* params, int64_t* tr_off,
+                          int64_t* pe_off) {
+  if (!prob || !params || !tr_off || !pe_off) return fail(nullptr, DGDFT_INVALID_ARG, "null argument");
+  Plan P;
+  std::string msg;
+  int r = build_plan(prob, params, P, msg);
+  if (r) return fail(nullptr, r, msg);
+  for (int k = 0; k < P.M; k++) {
+    tr_off[k] = P.desc[k].troff;
+    pe_off[k] = P.desc[k].peoff;
+  }
+  tr_off[P.M] = P.tot_tr;
+  pe_off[P.M] = P.tot_pe;
+  return DGDFT_OK;
+}
+
+int dgdft_dg_ingredients(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* prm,
+                         const dgdft_alb_result* res, double* kv, double* traces, double* proj, dgdft_stream stream) {
+  if (!ctx || !prob || !prm || !res || !res->coef || !kv || !traces || !proj)
+    return fail(ctx, DGDFT_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_OK(cudaSetDevice(ctx->device));
+  Plan P;
+  std::string msg;
+  int r = build_plan(prob, prm, P, msg);
+  if (r) return fail(ctx, r, msg);
+  const bool host = (prm->flags & DGDFT_HOST_BUFFERS) != 0;
+  if ((r = upload_plan(ctx, P, st))) return r;
+  Common c;
+  if ((r = get_common(ctx, P, std::max(2, prm->cheb_degree), 10, c))) return r;
+  const size_t M = P.M, L = P.L;
+  const double *eigvec, *coef, *vx;
+  if ((r = dg_eigvec(ctx, P, res, host, &eigvec))) return r;
+  if ((r = stage_in(ctx, host, "dg_coef", res->coef, M * L * L, &coef, st))) return r;
+  if ((r = stage_in(ctx, host, "vx_stage", prob->v_extra, P.tot_grid, &vx, st))) return r;
+  double *KV = kv, *TR = traces, *PE = proj;
+  if (host) {
+    WS(KV, "dg_kv", M * L * L * sizeof(double));
+    WS(TR, "dg_tr", std::max<long long>(1, P.tot_tr) * sizeof(double));
+    WS(PE, "dg_pe", std::max<long long>(1, P.tot_pe) * sizeof(double));
+  }
+  if ((r = dg_ingredients_dev(ctx, P, c, eigvec, coef, vx, KV, TR, PE, st))) return r;
+  if (host) {
+    CUDA_OK(cudaMemcpyAsync(kv, KV, M * L * L * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (P.tot_tr) CUDA_OK(cudaMemcpyAsync(traces, TR, P.tot_tr * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (P.tot_pe) CUDA_OK(cudaMemcpyAsync(proj, PE, P.tot_pe * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  CUDA_OK(cudaStreamSynchronize(st));
+  return DGDFT_OK;
+}
+
+int dgdft_dg_blocks(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* prm, const double* kv,
+                    const double* traces, const double* proj, double alpha, double* blocks, dgdft_stream stream) {
+  if (!ctx || !prob || !prm || !kv || !traces || !proj || !blocks) return fail(ctx, DGDFT_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_OK(cudaSetDevice(ctx->device));
+  Plan P;
+  std::string msg;
+  int r = build_plan(prob, prm, P, msg);
+  if (r) return fail(ctx, r, msg);
+  const bool host = (prm->flags & DGDFT_HOST_BUFFERS) != 0;
+  if ((r = upload_plan(ctx, P, st))) return r;
+  const size_t M = P.M, L = P.L;
+  const double *KV, *TR, *PE;
+  if ((r = stage_in(ctx, host, "dg_kv", kv, M * L * L, &KV, st))) return r;
+  if ((r = stage_in(ctx, host, "dg_tr", traces, P.tot_tr, &TR, st))) return r;
+  if ((r = stage_in(ctx, host, "dg_pe", proj, P.tot_pe, &PE, st))) return r;
+  double* out = blocks;
+  if (host) WS(out, "dg_blocks", size_t(P.n_stencil) * M * L * L * sizeof(double));
+  if ((r = dg_blocks_dev(ctx, P, prob, KV, TR, PE, alpha, out, st))) return r;
+  if (host)
+    CUDA_OK(cudaMemcpyAsync(blocks, out, size_t(P.n_stencil) * M * L * L * sizeof(double), cudaMemcpyDeviceToHost,
+                            st));
+  CUDA_OK(cudaStreamSynchronize(st));
+  return DGDFT_OK;
+}
+
 int dgdft_dg_assemble(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* prm,
                       const dgdft_alb_result* res, double alpha, double* blocks, dgdft_stream stream) {
   if (!ctx || !prob || !prm || !res || !blocks || !res->coef) return fail(ctx, DGDFT_INVALID_ARG, "null argument");
@@ -665,78 +846,17 @@ int dgdft_dg_assemble(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb
   Common c;
   if ((r = get_common(ctx, P, std::max(2, prm->cheb_degree), 10, c))) return r;
   const size_t M = P.M, L = P.L;
-  const double* eigvec = (host || res->eigvec == nullptr) ? nullptr : res->eigvec;
-  if (!eigvec) {
-    auto it = ctx->bufs.find("eigvec_ws");
-    if (it == ctx->bufs.end() || it->second.second < size_t(P.tot[OFF_E]) * sizeof(double))
-      return fail(ctx, DGDFT_INVALID_ARG, "no eigenvectors: pass result->eigvec or call dgdft_alb_generate first");
-    eigvec = (const double*)it->second.first;
-  }
-  const double* coef = res->coef;
-  const double* vx = prob->v_extra;
+  const double *eigvec, *coef, *vx;
+  if ((r = dg_eigvec(ctx, P, res, host, &eigvec))) return r;
+  if ((r = stage_in(ctx, host, "dg_coef", res->coef, M * L * L, &coef, st))) return r;
+  if ((r = stage_in(ctx, host, "vx_stage", prob->v_extra, P.tot_grid, &vx, st))) return r;
   double* out = blocks;
-  if (host) {
-    double *dc, *dv = nullptr;
-    WS(dc, "dg_coef", M * L * L * sizeof(double));
-    CUDA_OK(cudaMemcpyAsync(dc, coef, M * L * L * sizeof(double), cudaMemcpyHostToDevice, st));
-    coef = dc;
-    if (vx) {
-      WS(dv, "vx_stage", P.tot_grid * sizeof(double));
-      CUDA_OK(cudaMemcpyAsync(dv, vx, P.tot_grid * sizeof(double), cudaMemcpyHostToDevice, st));
-      vx = dv;
-    }
-    WS(out, "dg_blocks", size_t(P.n_stencil) * M * L * L * sizeof(double));
-  }
-  int* d_nb;
-  WS(d_nb, "dg_nb", std::max<size_t>(1, M * P.n_stencil) * sizeof(int));
-  {
-    std::vector<int> nb(M * P.n_stencil);
-    for (size_t k = 0; k < M; k++)
-      for (int s = 0; s < P.n_stencil; s++) nb[k * P.n_stencil + s] = P.n_stencil > 1 ? prob->neighbors[k * P.n_stencil + s] : int(k);
-    CUDA_OK(cudaMemcpyAsync(d_nb, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-  }
-  BatchArgs b{P.d_desc, nullptr, P.M};
-  CUDA_OK(cudaMemsetAsync(c.flags, 0, M * sizeof(int), st));
-  launch_setup_v(b, P.d_boxes, P.d_dtab, vx, P.r_cut, c.V64, c.V32, c.flags, st);
-  // psi^Q = C^T Phi^Q (trig interpolant of the ALBs on Q), its restriction A to E
-  double *Psi, *D, *PsiE, *VE, *PE, *TR;
-  cplx<double>* S;
-  {
-    char* ar = arena(ctx, P, 4);
-    if (!ar) return fail(ctx, DGDFT_OUT_OF_MEMORY, "out of device memory: block arena");
-    Psi = (double*)ar;
-    D = (double*)(ar + 2 * size_t(P.tot[OFF_X]) * 4);
-  }
-  WS(PsiE, "PhiE", P.tot[OFF_FE] * sizeof(double));
-  WS(VE, "dg_ve", P.tot[OFF_VE] * sizeof(double));
+  if (host) WS(out, "dg_blocks", size_t(P.n_stencil) * M * L * L * sizeof(double));
+  double *PE, *TR;
   WS(PE, "dg_pe", std::max<long long>(1, P.tot_pe) * sizeof(double));
   WS(TR, "dg_tr", std::max<long long>(1, P.tot_tr) * sizeof(double));
-  WS(S, "S_spec", size_t(P.tot[OFF_S]) * sizeof(cplx<double>));
-  const long long* oe = P.d_off[OFF_E];
-  const long long* ofe = P.d_off[OFF_FE];
-  launch_rotate<double, double>(b, eigvec, oe, Psi, oe, NV_EIG, NV_ALB, 4, coef, P.L, nullptr, nullptr, nullptr,
-                                nullptr, P.L, st);
-  // kinetic: 1/2 sum_axes (d psi)_E^T (d psi)_E dV with spectral derivatives (Nyquist dropped)
-  CUDA_OK(cudaMemsetAsync(c.G1, 0, M * L * L * sizeof(double), st));
-  set_group_nvec(P, NV_ALB);
-  HxArgs ha = hx_args(P, nullptr, OFF_E, NV_ALB);
-  for (int axis = 0; axis < 3; axis++) {
-    launch_forward<double>(P.hx, ha, Psi, S, st);
-    launch_zline<double>(P.hx, ha, S, MULT_DX + axis, st);
-    launch_inverse_raw<double>(P.hx, ha, S, D, st);
-    launch_restrict(b, D, oe, PsiE, ofe, NV_ALB, st);
-    launch_gram<double>(b, PsiE, ofe, NV_ALB, PsiE, ofe, NV_ALB, 5, nullptr, nullptr, c.G1, P.L, st, 0.5);
-  }
-  // V_eff term: A diag(V_E) A^T dV with A = psi restricted to E
-  launch_restrict(b, c.V64, P.d_off[OFF_V], VE, P.d_off[OFF_VE], NV_ONE, st);
-  launch_restrict(b, Psi, oe, PsiE, ofe, NV_ALB, st);
-  launch_gram<double>(b, PsiE, ofe, NV_ALB, PsiE, ofe, NV_ALB, 5, VE, P.d_off[OFF_VE], c.G1, P.L, st);
-  // projector overlaps on E and face traces
-  if (P.tot_pe > 0) CUDA_OK(cudaMemsetAsync(PE, 0, P.tot_pe * sizeof(double), st));
-  launch_proj_overlap(b, P.d_boxes, P.d_dtab, PsiE, ofe, P.r_cut, P.n_proj_per_atom, PE, P.max_pe, st);
-  if (P.tot_tr > 0) launch_face_traces(b, Psi, oe, TR, st);
-  launch_dg_blocks(b, d_nb, P.n_stencil, TR, PE, P.d_boxes, P.n_proj_per_atom, c.G1, P.L, alpha, out, st);
-  CUDA_OK(cudaGetLastError());
+  if ((r = dg_ingredients_dev(ctx, P, c, eigvec, coef, vx, c.G1, TR, PE, st))) return r;
+  if ((r = dg_blocks_dev(ctx, P, prob, c.G1, TR, PE, alpha, out, st))) return r;
   if (host)
     CUDA_OK(cudaMemcpyAsync(blocks, out, size_t(P.n_stencil) * M * L * L * sizeof(double), cudaMemcpyDeviceToHost,
                             st));
