@@ -227,6 +227,49 @@ int dgdft_dg_ingredients(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_
 int dgdft_dg_blocks(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* params, const double* kv,
                     const double* traces, const double* proj, double alpha, double* blocks, dgdft_stream stream);
 
+/* Parameters of dgdft_dg_eigensolve.  Host memory. */
+typedef struct {
+  int n_states;              /* lowest eigenpairs wanted */
+  int n_blk;                 /* filter block, n_states <= n_blk <= min(96, N_b) */
+  int cheb_degree;           /* filter order m >= 2 */
+  double tol;                /* residual ||H c - eps c|| (Euclidean) of the first n_states Ritz pairs */
+  int max_iter;              /* cap on filter passes */
+  int lanczos_steps;         /* steps of the upper-bound estimate (0 = 10) */
+  uint64_t seed;             /* SplitMix64 state of the random start (element index 0) */
+} dgdft_dg_solve_params;
+
+/* Lowest eigenpairs of the assembled DG Hamiltonian (Eq. DGEigenvalue; the ALB basis is orthonormal, so
+ * the problem is the standard symmetric one) by Chebyshev-filtered subspace iteration (Alg. CheFSI, the
+ * paper's solver for H^DG), FP64.  H^DG is applied from `blocks` (DATA [M][n_stencil][L][L] as written
+ * by dgdft_dg_assemble: block (k, s) couples the test ALBs of element k with the trial ALBs of
+ * neighbors[k][s]), never formed.  The basis index runs over the elements in order, n_alb[k] functions
+ * each (N_b = sum n_alb).  Outputs (DATA): eigval [n_blk] ascending, resid [n_blk], eigvec [n_blk][N_b]
+ * (rows orthonormal; may be NULL), iters [1] filter passes.  Returns DGDFT_OK, DGDFT_NOT_CONVERGED
+ * (outputs written), DGDFT_CHOLESKY_FAIL, DGDFT_BAD_INPUT, DGDFT_INVALID_ARG (sizes), DGDFT_UNSUPPORTED
+ * (N_b >= 2^24), DGDFT_OUT_OF_MEMORY, DGDFT_CUDA_ERROR. */
+int dgdft_dg_eigensolve(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* params,
+                        const double* blocks, const dgdft_dg_solve_params* solve, double* eigval, double* resid,
+                        double* eigvec, int* iters, dgdft_stream stream);
+
+/* Electron density, band energy and Hellmann-Feynman forces of the DG solution (Eq. density with the
+ * diagonal blocks of the density matrix, Eq. densitymatrix; Eq. DGvar on the DG eigenpairs, which is the
+ * band energy sum_i 2 f_i eps_i; Eq. hfforce for the wells and projectors of this model, at fixed ALBs).
+ *   result     the dgdft_alb_generate result whose ALBs (result->alb) span the DG basis
+ *   eigval     DATA [n] DG eigenvalues (e.g. from dgdft_dg_eigensolve), eigvec DATA [n][N_b] their
+ *              orthonormal coefficient rows in the ALB basis (elements in order, n_alb[k] each)
+ *   n          states used (1..96); f_i Fermi-Dirac at kT with mu fixed by sum_i 2 f_i = n_electrons
+ *   rho        DATA [total points of all domains]: sum_i 2 f_i psi_i(r)^2 at the points of every E_k (0
+ *              elsewhere)
+ *   energy_mu  DATA [2]: the band energy and mu
+ *   grad_R     DATA [n_atoms][3] or NULL: dE/dR_I at fixed ALBs (the force is its negative), including the
+ *              term that keeps the electron count fixed
+ * Device buffers only (DGDFT_HOST_BUFFERS returns DGDFT_UNSUPPORTED).  DGDFT_BAD_INPUT when the highest of
+ * the n states is occupied (f >= 1e-12). */
+int dgdft_dg_density(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* params,
+                     const dgdft_alb_result* result, const double* eigval, const double* eigvec, int n,
+                     double n_electrons, double kT, double* rho, double* energy_mu, double* grad_R,
+                     dgdft_stream stream);
+
 /* Band energy E_k = sum_j 2 f_j lambda_j (f Fermi-Dirac at kT, mu_k fixed by
  * n_electrons[k], a host array) and its gradient: energy DATA [M],
  * grad_v DATA [total points of all domains] (dE/dV at each grid point,

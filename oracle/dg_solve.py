@@ -65,3 +65,65 @@ def dg_density(prob, sols, n_alb, eps, C, n_electrons, kT):
         psi = C[:, off[k]:off[k + 1]] @ A                 # [n, N_E]
         rho.append((2.0 * f[:, None] * psi * psi).sum(axis=0))
     return rho, mu, float((2.0 * f * eps).sum())
+
+
+def dg_band_gradient(prob, sols, n_alb, eps, C, n_electrons, kT):
+    """Fermi-smeared DG band energy and its derivative with respect to the atom positions at fixed ALBs
+    (the DG form of the Hellmann-Feynman force, Eq. hfforce; the force is minus this gradient).
+
+    E = sum_i 2 f_i eps_i over the DG eigenpairs (eps [n], rows of C [n, N_b] orthonormal), which equals
+    Eq. DGvar evaluated on psi_i = sum_{k,a} C_{i,ka} phi_{k,a}.  With the ALBs held fixed, H^DG depends on
+    R_I only through the local well V_I in the V_eff term and the projectors b_{I,l}, so
+
+        dE/dR_I = sum_i w_i [ <psi_i, (dV_I/dR_I) psi_i>_T
+                              + 2 sum_l gamma_l <psi_i, b_l>_T <psi_i, db_l/dR_I>_T ],
+        w_i = 2 [f_i + f'_i (eps_i - mu_bar)]
+
+    (the mu_bar term keeps the electron count fixed, as in oracle/grad.py).  The integrals over T run over
+    the elements: psi_i on E_k is sum_a C_{i,ka} phi_{k,a}.  Returns (E, mu, grad_R [n_atoms, 3])."""
+    from .grad import band_energy_weights, _dgauss_taper
+    from .local_operator import displacements, projector_norms, taper
+    eps = np.asarray(eps, dtype=np.float64)
+    E, mu, w, f = band_energy_weights(eps, float(n_electrons), kT)
+    off = np.concatenate([[0], np.cumsum(np.asarray(n_alb, dtype=np.int64))])
+    grad_R = np.zeros((prob.n_atoms, 3))
+    npa = prob.n_proj_per_atom
+    pb = np.zeros((prob.n_atoms, max(npa, 1), len(eps)))
+    pdb = np.zeros((prob.n_atoms, max(npa, 1), 3, len(eps)))
+    for k in range(prob.n_elem):
+        dom = int(prob.elem_dom[k])
+        dV = float(np.prod(prob.dom_h[dom]))
+        En = prob.elem_En[k]
+        gE = [np.mod(prob.elem_E0[k][a] + np.arange(int(En[a])), prob.dom_n[dom][a]) for a in range(3)]
+        Psi = C[:, off[k]:off[k + 1]] @ sols[k]["A"]            # [n, N_E]: psi_i on E_k
+        rho_w = (w[:, None] * Psi * Psi).sum(axis=0)
+        for a in range(prob.n_atoms):
+            if int(prob.atom_dom[a]) != dom:
+                continue
+            DX, DY, DZ = displacements(prob, dom, gE[0], gE[1], gE[2], prob.atom_pos[a])
+            if not np.any(taper(np.sqrt(DX * DX + DY * DY + DZ * DZ) / prob.r_cut) > 0):
+                continue
+            _, dgw = _dgauss_taper(DX, DY, DZ, prob.well_width[a], prob.r_cut)
+            for ax in range(3):
+                grad_R[a, ax] += prob.well_depth[a] * float((rho_w * dgw[ax].ravel()).sum()) * dV
+            if npa == 0:
+                continue
+            sig = prob.proj_width[a]
+            g, dgp = _dgauss_taper(DX, DY, DZ, sig, prob.r_cut)
+            ns, np_ = projector_norms(sig)
+            disp = (DX, DY, DZ)
+            b = [ns * g] + ([np_ * disp[0] * g, np_ * disp[1] * g, np_ * disp[2] * g] if npa == 4 else [])
+            for l in range(npa):
+                pb[a, l] += Psi @ b[l].ravel() * dV
+                for ax in range(3):
+                    if l == 0:
+                        db = -ns * dgp[ax]
+                    else:
+                        beta = l - 1
+                        db = -np_ * ((g if beta == ax else 0.0) + disp[beta] * dgp[ax])
+                    pdb[a, l, ax] += Psi @ np.asarray(db).ravel() * dV
+    for a in range(prob.n_atoms):
+        for l in range(npa):
+            for ax in range(3):
+                grad_R[a, ax] += float((w * 2.0 * prob.proj_gamma[a, l] * pb[a, l] * pdb[a, l, ax]).sum())
+    return E, mu, grad_R

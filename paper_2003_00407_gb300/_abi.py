@@ -38,6 +38,11 @@ class AlbResult(C.Structure):
                 ("history", C.c_void_p)]
 
 
+class DGSolveParams(C.Structure):
+    _fields_ = [("n_states", C.c_int), ("n_blk", C.c_int), ("cheb_degree", C.c_int), ("tol", C.c_double),
+                ("max_iter", C.c_int), ("lanczos_steps", C.c_int), ("seed", C.c_uint64)]
+
+
 FUNCTIONS = {
     "dgdft_alb_query_sizes": (C.c_int, [C.POINTER(Problem), C.POINTER(AlbParams), PL]),
     "dgdft_ctx_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
@@ -59,6 +64,12 @@ FUNCTIONS = {
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dgdft_dg_blocks": (C.c_int, [C.c_void_p, C.POINTER(Problem), C.POINTER(AlbParams), C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
+    "dgdft_dg_eigensolve": (C.c_int, [C.c_void_p, C.POINTER(Problem), C.POINTER(AlbParams), C.c_void_p,
+                                      C.POINTER(DGSolveParams), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
+    "dgdft_dg_density": (C.c_int, [C.c_void_p, C.POINTER(Problem), C.POINTER(AlbParams), C.POINTER(AlbResult),
+                                   C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p]),
     "dgdft_stage_converged": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, PD, PI]),
     "dgdft_apply_hamiltonian_noalloc": (C.c_int, [C.POINTER(Problem), C.POINTER(AlbParams), C.c_void_p, C.c_void_p,
                                                   C.c_void_p]),

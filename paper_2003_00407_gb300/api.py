@@ -381,3 +381,49 @@ def result_subset(res: ALBResult, prob, params, elems, sub_prob, sub_params, pre
                     iters=res.iters[idx].contiguous(), status=res.status[idx].contiguous(), L=L, code=res.code)
     sub.struct = (m, sub.as_struct())
     return sub
+
+
+def dg_eigensolve(ctx: Context, prob, params, blocks: torch.Tensor, n_states: int, n_blk: int, *,
+                  cheb_degree=30, tol=1e-10, max_iter=200, lanczos_steps=10, seed=None, keep_vectors=True,
+                  allow_not_converged=False):
+    """Lowest eigenpairs of the assembled DG Hamiltonian from its stencil blocks (dgdft_dg_eigensolve).
+
+    Returns (eigval [n_blk], resid [n_blk], eigvec [n_blk, N_b] or None, passes) on the device."""
+    dev = torch.device("cuda", ctx.device)
+    m = Marshalled(prob, params, precision=_abi.FP64, cheb_degree=max(2, params.cheb_degree), tol=params.tol,
+                   max_iter=params.max_iter)
+    sp = _abi.DGSolveParams(n_states=int(n_states), n_blk=int(n_blk), cheb_degree=int(cheb_degree), tol=float(tol),
+                            max_iter=int(max_iter), lanczos_steps=int(lanczos_steps),
+                            seed=int(params.seed if seed is None else seed))
+    Nb = int(np.sum(params.n_alb))
+    ev = torch.empty(n_blk, dtype=torch.float64, device=dev)
+    rs = torch.empty(n_blk, dtype=torch.float64, device=dev)
+    vec = torch.empty(n_blk, Nb, dtype=torch.float64, device=dev) if keep_vectors else None
+    it = torch.zeros(1, dtype=torch.int32, device=dev)
+    blocks = blocks.contiguous()
+    allow = (0, _abi.NOT_CONVERGED) if allow_not_converged else (0,)
+    ctx.check(ctx.lib.dgdft_dg_eigensolve(ctx.h, C.byref(m.prob), C.byref(m.params), C.c_void_p(blocks.data_ptr()),
+                                          C.byref(sp), C.c_void_p(ev.data_ptr()), C.c_void_p(rs.data_ptr()),
+                                          C.c_void_p(vec.data_ptr() if vec is not None else 0),
+                                          C.c_void_p(it.data_ptr()), _stream()), allow)
+    return ev, rs, vec, int(it.item())
+
+
+def dg_density(ctx: Context, prob, params, res: ALBResult, eigval: torch.Tensor, eigvec: torch.Tensor, n: int,
+               n_electrons: float, kT: float, forces=True):
+    """(rho [total grid points], band energy, mu, grad_R [n_atoms, 3] or None) of the DG solution
+    (dgdft_dg_density): density from the diagonal density-matrix blocks, band energy, dE/dR at fixed ALBs."""
+    m, s = res.struct
+    dev = torch.device("cuda", ctx.device)
+    rho = torch.empty(int(prob.v_extra.size), dtype=torch.float64, device=dev)
+    em = torch.empty(2, dtype=torch.float64, device=dev)
+    gR = torch.empty(max(1, prob.n_atoms), 3, dtype=torch.float64, device=dev) if forces else None
+    ev = eigval.contiguous()
+    vec = eigvec.contiguous()
+    ctx.check(ctx.lib.dgdft_dg_density(ctx.h, C.byref(m.prob), C.byref(m.params), C.byref(s),
+                                       C.c_void_p(ev.data_ptr()), C.c_void_p(vec.data_ptr()), int(n),
+                                       float(n_electrons), float(kT), C.c_void_p(rho.data_ptr()),
+                                       C.c_void_p(em.data_ptr()), C.c_void_p(gR.data_ptr() if forces else 0),
+                                       _stream()))
+    e = em.cpu().numpy()
+    return rho, float(e[0]), float(e[1]), (gR[:prob.n_atoms] if forces else None)

@@ -14,13 +14,7 @@
 #include "kernels.h"
 #include "plan.h"
 
-struct dgdft_ctx {
-  int device = 0;
-  std::string err;
-  std::map<std::string, std::pair<void*, size_t>> bufs;
-  bool tw_ready = false;
-  int* h_active = nullptr;  // pinned readback: active-element count and the max residual
-};
+#include "context.h"
 
 namespace dgdft {
 

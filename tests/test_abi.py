@@ -102,7 +102,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     if cc is None:
         pytest.skip("no host C compiler")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    structs = {"dgdft_problem": _abi.Problem, "dgdft_alb_params": _abi.AlbParams, "dgdft_alb_result": _abi.AlbResult}
+    structs = {"dgdft_problem": _abi.Problem, "dgdft_alb_params": _abi.AlbParams, "dgdft_alb_result": _abi.AlbResult,
+               "dgdft_dg_solve_params": _abi.DGSolveParams}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dgdft.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')

@@ -56,20 +56,32 @@ def _block_measures(p, q, blocks, gold):
     return w_abs, w_rel
 
 
+_C2 = {}
+
+
+def _c2(ctx, precision):
+    """ALB generation + DG blocks of the c2 slab (cached per precision for the tests of this module)."""
+    if precision not in _C2:
+        from paper_2003_00407_gb300 import api
+        from workloads import make_config
+        w = make_config(2)
+        p, q = w.problem, w.params
+        if precision == 0:
+            res = api.alb_generate(ctx, p, q, precision=0, cheb_degree=40, tol=1e-10, max_iter=200)
+        else:
+            res = api.alb_generate(ctx, p, q, precision=1, cheb_degree=80, tol=1e-8, max_iter=60)
+        st = res.status.cpu().numpy()
+        assert np.count_nonzero(st) == 0, np.nonzero(st)
+        _C2[precision] = (w, res, api.dg_assemble(ctx, p, q, res, w.alpha))
+    return _C2[precision]
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_c2_assembled_dg_eigenvalues(ctx, precision):
-    from paper_2003_00407_gb300 import api
-    from workloads import make_config
     gold = json.load(open(os.path.join(HERE, "c2_dg.json")))
-    w = make_config(2)
+    w, res, blocks_t = _c2(ctx, precision)
     p, q = w.problem, w.params
-    if precision == 0:
-        res = api.alb_generate(ctx, p, q, precision=0, cheb_degree=40, tol=1e-10, max_iter=200)
-    else:
-        res = api.alb_generate(ctx, p, q, precision=1, cheb_degree=80, tol=1e-8, max_iter=60)
-    st = res.status.cpu().numpy()
-    assert np.count_nonzero(st) == 0, np.nonzero(st)
-    blocks = api.dg_assemble(ctx, p, q, res, w.alpha).cpu().numpy()
+    blocks = blocks_t.cpu().numpy()
     H = _dense(p, blocks, q.n_alb)
     asym = np.abs(H - H.T).max()
     lam = np.linalg.eigvalsh(0.5 * (H + H.T))[:64]
@@ -152,3 +164,76 @@ def test_uneven_multipass_shape_live_subspace(ctx):
     print("uneven 40x40x48 element", k, "eigenvalue error", de, "ALB sine", sine)
     assert de <= 1e-6
     assert sine <= 1e-5
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c2_dg_eigensolve_on_the_gpu(ctx, precision):
+    """NEXT step of the method on the GPU: CheFSI on the assembled H^DG (Eq. DGEigenvalue, Alg. CheFSI)
+    from the GPU blocks, without forming H^DG: the lowest 64 eigenvalues against the oracle golden
+    (1e-6 Ha for FP64 ALBs, the mixed bound 1e-5 Ha otherwise) and against the dense eigensolve of the
+    same blocks (1e-9 Ha); the eigenvectors are orthonormal with residuals at the tolerance."""
+    from paper_2003_00407_gb300 import api
+    gold = json.load(open(os.path.join(HERE, "c2_dg.json")))
+    w, res, blocks = _c2(ctx, precision)
+    p, q = w.problem, w.params
+    ev, rs, vec, passes = api.dg_eigensolve(ctx, p, q, blocks, 64, 80, cheb_degree=30, tol=1e-9, max_iter=300)
+    ev, rs, vec = ev.cpu().numpy(), rs.cpu().numpy(), vec.cpu().numpy()
+    H = _dense(p, blocks.cpu().numpy(), q.n_alb)
+    lam = np.linalg.eigvalsh(0.5 * (H + H.T))[:64]
+    d_dense = np.abs(ev[:64] - lam).max()
+    d_gold = np.abs(ev[:64] - np.array(gold["lowest_eigenvalues"])).max()
+    orth = np.abs(vec @ vec.T - np.eye(80)).max()
+    r = np.linalg.norm(vec[:64] @ H.T - ev[:64, None] * vec[:64], axis=1).max()
+    print(f"DG eigensolve precision {precision}: passes {passes}, vs dense {d_dense:.2e}, vs golden {d_gold:.2e}, "
+          f"orthonormality {orth:.1e}, residual {r:.1e}")
+    assert rs[:64].max() <= 1e-9 and r <= 1e-8
+    assert orth <= 1e-10
+    assert d_dense <= 1e-9
+    assert d_gold <= (1e-6 if precision == 0 else 1e-5)
+
+
+def test_whole_box_dg_eigensolve_matches_the_oracle_solver(ctx):
+    """2x2 elements whose extended element is the whole box (9-block stencil): the GPU DG eigensolve on
+    the GPU blocks against the oracle's CheFSI on the oracle blocks (oracle/dg_solve.py), 1e-6 Ha."""
+    from paper_2003_00407_gb300 import api
+    from oracle import driver, dg_solve
+    from workloads.configs import make_slab
+    from workloads.problem import STENCIL_XY9
+    w = make_slab(2, 2, (6, 6, 12), (12, 12, 12), 0.5, 10, 8, 3, stencil=STENCIL_XY9, width=0.7, proj_width=0.7,
+                  r_cut=2.8, lattice=1, jitter=0.3)
+    p, q = w.problem, w.params
+    sols = {k: driver.solve_element(p, q, k, dense_route=True) for k in range(p.n_elem)}
+    blocks_o, _ = driver.dg_assemble(p, sols, 7.0)
+    ref = dg_solve.dg_eigenpairs(p, blocks_o, q.n_alb, 12, 16, 20, 1e-11, 500, 99)
+    res = api.alb_generate(ctx, p, q, precision=0, cheb_degree=12, tol=1e-10, max_iter=400)
+    blocks = api.dg_assemble(ctx, p, q, res, 7.0)
+    ev, rs, vec, passes = api.dg_eigensolve(ctx, p, q, blocks, 12, 16, cheb_degree=20, tol=1e-10, max_iter=500,
+                                            seed=99)
+    d = np.abs(ev.cpu().numpy()[:12] - ref["theta"][:12]).max()
+    print("whole-box DG eigensolve: passes", passes, "vs oracle solver", d)
+    assert d <= 1e-6
+
+
+def test_c2_dg_density_energy_and_forces(ctx):
+    """The DG solution of the c2 slab on the GPU (64 states, 32 electrons, kT 0.01 Ha) from FP64 ALBs:
+    band energy and mu within 1e-6 Ha of the oracle golden, the density at 64 grid points within 1e-6 of
+    its maximum, the charge within 1e-9, the Hellmann-Feynman gradient within 1e-5 of its largest entry."""
+    from paper_2003_00407_gb300 import api
+    gold = json.load(open(os.path.join(HERE, "c2_dg.json")))["dg_solution"]
+    w, res, blocks = _c2(ctx, 0)
+    p, q = w.problem, w.params
+    n = gold["n_states"]
+    ev, rs, vec, _ = api.dg_eigensolve(ctx, p, q, blocks, n, 80, cheb_degree=30, tol=1e-9, max_iter=300)
+    rho, E, mu, gR = api.dg_density(ctx, p, q, res, ev[:n], vec[:n], n, gold["n_electrons"], gold["kT"])
+    rho, gR = rho.cpu().numpy(), gR.cpu().numpy()
+    dV = float(np.prod(p.dom_h[0]))
+    pts = np.array(gold["rho_points"])
+    d_rho = np.abs(rho[pts] - np.array(gold["rho_at_points"])).max() / gold["rho_max"]
+    ref_R = np.array(gold["grad_R"])
+    d_R = np.abs(gR - ref_R).max() / np.abs(ref_R).max()
+    print(f"c2 DG solution: band energy {E:.9f} vs {gold['band_energy']:.9f}, mu {mu:.7f} vs {gold['mu']:.7f}, "
+          f"rho rel {d_rho:.2e}, grad_R rel {d_R:.2e}, charge {rho.sum() * dV:.10f}")
+    assert abs(rho.sum() * dV - gold["n_electrons"]) <= 1e-9
+    assert abs(E - gold["band_energy"]) <= 1e-6 and abs(mu - gold["mu"]) <= 1e-6
+    assert d_rho <= 1e-6
+    assert d_R <= 1e-5

@@ -55,3 +55,42 @@ def test_density_integrates_to_the_electron_count_and_matches_the_density_matrix
     f = fermi(eps[:10], mu, kT)
     D = (C.T * (2.0 * f)) @ C
     assert abs(e_band - np.trace(H @ D)) <= 1e-10 * max(1.0, abs(e_band))
+
+
+def _band_energy_fixed_albs(w, sols, n_states, n_el, kT, alpha=20.0):
+    """E_DG of the lowest n_states DG eigenpairs with the ALBs of `sols` held fixed (the problem's atoms
+    may have moved): H^DG re-assembled from the same ALBs, eigh, Fermi-smeared band energy."""
+    from oracle.grad import band_energy_weights
+    p = w.problem
+    ingr = [dg.element_ingredients(p, k, sols[k]["X"][:sols[k]["n_eig"]], sols[k]["C"], sols[k]["A"])
+            for k in range(p.n_elem)]
+    blocks, _ = dg.assemble(p, ingr, alpha)
+    eps = np.linalg.eigvalsh(dg.dense(p, blocks, w.params.n_alb))[:n_states]
+    return band_energy_weights(eps, n_el, kT)[0]
+
+
+def test_dg_band_gradient_matches_central_differences():
+    """dE_DG/dR at fixed ALBs (the DG Hellmann-Feynman force, Eq. hfforce) against central differences of
+    the re-assembled, re-diagonalised DG band energy (step 1e-4 bohr, error O(1e-8))."""
+    import copy
+    w, blocks = _case()
+    p, n_alb = w.problem, w.params.n_alb
+    sols = _sols_dense(w)
+    H = dg.dense(p, blocks, n_alb)
+    eps, V = np.linalg.eigh(H)
+    n, n_el, kT = 12, 6.0, 0.02
+    E, mu, gR = dg_solve.dg_band_gradient(p, sols, n_alb, eps[:n], V[:, :n].T, n_el, kT)
+    assert abs(E - _band_energy_fixed_albs(w, sols, n, n_el, kT)) <= 1e-12
+    step = 1e-4
+    worst = 0.0
+    for a in range(p.n_atoms):
+        for ax in range(3):
+            Es = []
+            for sgn in (1, -1):
+                w2 = copy.deepcopy(w)
+                w2.problem.atom_pos[a, ax] += sgn * step
+                Es.append(_band_energy_fixed_albs(w2, sols, n, n_el, kT))
+            fd = (Es[0] - Es[1]) / (2 * step)
+            worst = max(worst, abs(fd - gR[a, ax]))
+    assert worst <= 1e-6 * max(1.0, np.abs(gR).max()), (worst, np.abs(gR).max())
+    assert np.abs(gR).max() > 1e-3        # the test moves something
