@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--config", type=int, default=5)
-    ap.add_argument("--degree", type=int, default=80)
+    ap.add_argument("--degree", type=int, default=100)
     ap.add_argument("--max-iter", type=int, default=60)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--fp64-elements", type=int, default=128, help="elements in the FP64 GPU sample (0 = skip)")

@@ -91,10 +91,18 @@ int upload_plan(dgdft_ctx* ctx, Plan& P, cudaStream_t st) {
   if ((r = up("p_desc", P.desc.data(), P.desc.size() * sizeof(ElemDesc), (void**)&P.d_desc))) return r;
   if ((r = up("p_boxes", P.boxes.data(), P.boxes.size() * sizeof(AtomBox), (void**)&P.d_boxes))) return r;
   if ((r = up("p_dtab", P.dtab.data(), P.dtab.size() * sizeof(double), (void**)&P.d_dtab))) return r;
-  if ((r = up("p_dtab32", P.dtab32.data(), P.dtab32.size() * sizeof(float), (void**)&P.d_dtab32))) return r;
   if ((r = up("p_fatoms", P.fatoms.data(), std::max<size_t>(1, P.fatoms.size()) * sizeof(FusedAtomRec),
               (void**)&P.d_fatoms)))
     return r;
+  {
+    // compact projector-point lists of the Q boxes (read by the fused kernel)
+    const size_t nq = size_t(std::max(1, P.n_qboxes));
+    P.plist.g = (float*)ws(ctx, "p_plist_g", nq * kProjCap * sizeof(float));
+    P.plist.w = (unsigned*)ws(ctx, "p_plist_w", nq * kProjCap * sizeof(unsigned));
+    P.plist.n = (int*)ws(ctx, "p_plist_n", nq * sizeof(int));
+    if (!P.plist.g || !P.plist.w || !P.plist.n) return fail(ctx, DGDFT_OUT_OF_MEMORY, "workspace allocation failed: p_plist");
+    if (P.n_qboxes > 0) launch_build_proj_lists(P.d_fatoms, P.d_dtab, P.n_qboxes, P.r_cut, P.plist, st);
+  }
   const char* names[kOffKinds] = {"p_ox", "p_oe", "p_oa", "p_ov", "p_os", "p_ofe", "p_ove"};
   for (int i = 0; i < kOffKinds; i++)
     if ((r = up(names[i], P.off[i].data(), P.off[i].size() * sizeof(long long), (void**)&P.d_off[i]))) return r;
@@ -122,7 +130,7 @@ HxArgs hx_args(const Plan& P, const int* flags, int kind, int nvec_mode) {
   a.n_proj_per_atom = P.n_proj_per_atom;
   a.r_cut = P.r_cut;
   a.fatoms = P.d_fatoms;
-  a.dtab32 = P.d_dtab32;
+  a.plist = P.plist;
   return a;
 }
 

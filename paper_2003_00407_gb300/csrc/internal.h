@@ -40,14 +40,27 @@ struct ElemDesc {
   float kscale[3];  // 1/2 (2 pi / (n_a h_a))^2 / N: kinetic multiplier per m_a^2
 };
 
-// FP32 record of an atom box meeting Q, for the fused Chebyshev kernel
-// (parallel to the Q boxes; toff is relative to the element's tab_off).
+// Record of an atom box meeting Q for the fused FP32 Chebyshev kernel (parallel to the Q boxes).
+// The kernel reads the box's projector points from a compact list (see ProjList); the record holds what
+// turns the list's moments into the four projector overlaps and back.
 struct FusedAtomRec {
-  int s[3], l[3];
-  int toff, pad;
+  int s[3], l[3];   // box start (cyclic, Q-local) and extent per axis
+  int dtab;         // first entry of the box's displacement tables in the plan's dtab (x, then y, then z)
+  int qn[3];        // Q extent of the element (smem row layout of the fused kernel)
   float inv2s2;     // 1 / (2 sigma^2) of the projector radial Gaussian
   float c[4];       // gamma_l N_l^2 dV for s, px, py, pz (0 when absent)
-  float pad2;
+  float d0[3];      // displacement (bohr) of the box's first point along x, y, z; point i: d0 + i h
+};
+
+// Compact projector-point lists, one slot of kProjCap entries per fused atom record: the box points of
+// Q inside the support ball, in (z, y, x) order.  g = exp(-d^2 / 2 sigma^2) (1 - d^2/r_cut^2)^3 and
+// w = (smem float index of the point in the fused kernel's row layout) | ix << 16 | iy << 20 | iz << 24;
+// n[r] = number of points of record r.
+constexpr int kProjCap = 4096;
+struct ProjList {
+  float* g;
+  unsigned* w;
+  int* n;
 };
 
 // An atom whose support box meets a region (Q or E) of one element.  The box

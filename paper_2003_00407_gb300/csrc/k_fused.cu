@@ -5,8 +5,8 @@
 // whole step, so the vector is read once from HBM (plus an L2 re-read in the
 // epilogue), y_prev is read once and y_out written once.
 // Phases (one __syncthreads between each):
-//   1 x-rows: load, projector overlaps <b, y>, R2C along x (length QX via a
-//     complex transform of QX/2), store the row's half spectrum;
+//   1 x-rows: load, projector overlaps <b, y> (from the element's compact lists of the projector
+//     points), R2C along x (length QX via a complex transform of QX/2), store the row's half spectrum;
 //   2 y-lines: forward transform along y;
 //   3 z-lines: forward along z, kinetic multiplier, inverse along z;
 //   4 y-lines: inverse along y;
@@ -101,11 +101,10 @@ struct FusedArgs {
   const int* elems;
   const int* flags;
   const FusedAtomRec* fatoms;
-  const float* dtab32;
+  ProjList plist;
   const long long* xo;
   int nvec_mode;
   int npa;
-  float inv_rc2;
 };
 
 // 28 warps (7 per scheduler, at most 72 registers a thread): more resident warps hide the shared-memory
@@ -113,7 +112,6 @@ struct FusedArgs {
 constexpr int kFusedThreads = 896;
 constexpr int kFusedWarps = kFusedThreads / 32;
 constexpr int kFusedMaxAtoms = 96;
-constexpr int kFusedMaxTab = 3072;   // floats of displacement and x-factor tables per CTA (at most)
 constexpr int kSmemOptin = 232448;   // opt-in shared memory per block (sm_103)
 constexpr int kFusedStatic = 8192;   // bound on the kernel's static shared memory
 
@@ -126,175 +124,86 @@ constexpr int kFusedStatic = 8192;   // bound on the kernel's static shared memo
   X(40, 24, 32) X(32, 40, 32)
 
 template <int QX, int QY, int QZ> constexpr int fused_spectrum_bytes() { return (QX / 2 + 1) * QY * QZ * 8; }
-// displacement-table floats that fit beside the half spectrum
-template <int QX, int QY, int QZ> constexpr int fused_tab_floats() {
-  constexpr int room = (kSmemOptin - kFusedStatic - fused_spectrum_bytes<QX, QY, QZ>()) / 4;
-  return room < kFusedMaxTab ? room : kFusedMaxTab;
-}
 template <int QX, int QY, int QZ> constexpr int fused_smem_bytes() {
-  static_assert(fused_tab_floats<QX, QY, QZ>() >= 512, "half spectrum too large for shared memory");
-  return fused_spectrum_bytes<QX, QY, QZ>() + fused_tab_floats<QX, QY, QZ>() * 4;
+  static_assert(fused_spectrum_bytes<QX, QY, QZ>() + kFusedStatic <= kSmemOptin, "half spectrum too large");
+  static_assert((QX / 2 + 1) * 2 * QY * QZ <= 65536, "row layout exceeds the 16-bit point index of the lists");
+  return fused_spectrum_bytes<QX, QY, QZ>();
 }
 
-// Nonlocal work item: two z-slices (iz = 2 zq + h, h = lane / 16) of one atom's box; each
-// lane owns one x-row (iy = lane % 16) and walks its 16 points.  The radial factor is
-// g = exp(-d^2 / 2 sigma^2) (1 - d^2/rc^2)^3 inside r_cut, evaluated as
-// e_row e_x max(R_row - t_x, 0)^3 with e_x = exp(-dx^2 / 2 sigma^2), t_x = dx^2 / rc^2 from the
-// atom's x-factor table (held in registers while the warp stays on the atom),
-// R_row = 1 - (dy^2 + dz^2) / rc^2.  The second half-warp walks the points rotated by one
-// (point j = (i + h) mod 16 at step i): with an even row pitch the two z-slices then fall on
-// odd and even banks, so the row accesses are free of bank conflicts.
-struct NlAtom {
-  float e[16], t[16];   // x factors in the lane's walk order
-};
-struct NlRow {
-  float erow, rem, dy, dz;
-  float* row;           // the row slot in the shared buffer
-  bool ok;
-};
-
-__device__ __forceinline__ void nl_atom(const float* xf, NlAtom& x) {
-  const int h = (threadIdx.x & 31) >> 4;
-#pragma unroll
-  for (int i = 0; i < 16; i++) {
-    const int j = (i + h) & 15;
-    x.e[i] = xf[j];
-    x.t[i] = xf[16 + j];
-  }
+// ---- projector phases from the compact point lists ----
+// List entry p of atom a: g = radial factor, w = smem float index | ix << 16 | iy << 20 | iz << 24.
+// Overlaps: warp w takes a contiguous, equal share of all the element's points (atom-major), lanes on
+// consecutive points, 8 entries loaded ahead; per atom the moments S0 = sum g y, S_x = sum g y ix, ...
+// give sum g y (d0_x + ix h_x) etc.  Application: row value += g (B0 + Bx ix + By iy + Bz iz) through
+// shared atomics, with B the atom's coefficients.
+__device__ __forceinline__ float small_float(unsigned v) {   // exact float of v < 2^23
+  return __int_as_float(0x4B000000u | v) - 8388608.f;
 }
 
-template <int QY, int QZ>
-__device__ __forceinline__ void nl_row(const FusedAtomRec& at, int zq, const float* tabs, float inv_rc2, float* buf,
-                                       int pitch, NlRow& r) {
-  const int lane = threadIdx.x & 31;
-  const int h = lane >> 4, iy = lane & 15, iz = 2 * zq + h;
-  r.ok = iy < at.l[1] && iz < at.l[2];
-  r.dy = 0.f;
-  r.dz = 0.f;
-  if (r.ok) {
-    r.dy = tabs[at.toff + at.l[0] + iy];
-    r.dz = tabs[at.toff + at.l[0] + at.l[1] + iz];
-  }
-  const float dyz2 = r.dy * r.dy + r.dz * r.dz;
-  r.rem = 1.f - dyz2 * inv_rc2;
-  r.ok = r.ok && r.rem > 0.f;
-  r.erow = r.ok ? __expf(-dyz2 * at.inv2s2) : 0.f;
-  int yy = at.s[1] + iy;
-  if (yy >= QY) yy -= QY;
-  int zz = at.s[2] + iz;
-  if (zz >= QZ) zz -= QZ;
-  r.row = buf + (zz * QY + yy) * pitch;
-}
-
-// Overlap sums of one item (s, x, y, z components without the norms), reduced over the warp:
-// sum g y, sum g y dx (= dx0 sum g y + hx sum j g y), sum g y dy, sum g y dz.
-template <int QX>
-__device__ __forceinline__ void nl_proj(const FusedAtomRec& at, const NlAtom& x, const NlRow& r, float dx0,
-                                        float hx, float acc[4]) {
-  const int h = (threadIdx.x & 31) >> 4;
-  float s = 0.f, si = 0.f;
-  if (r.ok) {
-    if (at.s[0] + 17 <= QX) {
-      // no wrap: point i < 15 of the walk sits at base[i]; the last one at base[15] or row[s]
-      const float* base = r.row + at.s[0] + h;
-#pragma unroll
-      for (int i = 0; i < 15; i++) {
-        const float u = fmaxf(r.rem - x.t[i], 0.f);
-        const float gy = x.e[i] * (u * u * u) * base[i];
-        s += gy;
-        si = fmaf(gy, float(i), si);
-      }
-      si = fmaf(float(h), s, si);
-      const float u = fmaxf(r.rem - x.t[15], 0.f);
-      const float gy = x.e[15] * (u * u * u) * (h ? r.row[at.s[0]] : base[15]);
-      s += gy;
-      si = fmaf(gy, h ? 0.f : 15.f, si);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 16; i++) {
-        const int j = (i + h) & 15;
-        int xx = at.s[0] + j;
-        if (xx >= QX) xx -= QX;
-        const float u = fmaxf(r.rem - x.t[i], 0.f);
-        const float gy = x.e[i] * (u * u * u) * r.row[xx];
-        s += gy;
-        si = fmaf(gy, float(j), si);
-      }
-    }
-    s *= r.erow;
-    si *= r.erow;
-  }
-  float sx = fmaf(dx0, s, hx * si), sy = s * r.dy, sz = s * r.dz;
-  for (int o = 16; o > 0; o >>= 1) {
-    s += __shfl_xor_sync(0xffffffffu, s, o);
-    sx += __shfl_xor_sync(0xffffffffu, sx, o);
-    sy += __shfl_xor_sync(0xffffffffu, sy, o);
-    sz += __shfl_xor_sync(0xffffffffu, sz, o);
-  }
-  acc[0] = s; acc[1] = sx; acc[2] = sy; acc[3] = sz;
-}
-
-// Application of one item: row += g (c_s + c_x dx + c_y dy + c_z dz) = g (b0 + b1 j).
-template <int QX>
-__device__ __forceinline__ void nl_apply(const FusedAtomRec& at, const NlAtom& x, const NlRow& r, float dx0,
-                                         float hx, const float* coef) {
-  if (!r.ok) return;
-  const int h = (threadIdx.x & 31) >> 4;
-  const float b0 = r.erow * (coef[0] + coef[2] * r.dy + coef[3] * r.dz + coef[1] * dx0);
-  const float b1 = r.erow * coef[1] * hx;
-  if (at.s[0] + 17 <= QX) {
-    float* base = r.row + at.s[0] + h;
-    const float b0h = fmaf(b1, float(h), b0);
-#pragma unroll
-    for (int i = 0; i < 15; i++) {
-      const float u = fmaxf(r.rem - x.t[i], 0.f);
-      const float g = x.e[i] * (u * u * u);
-      if (g != 0.f) atomicAdd(base + i, g * fmaf(b1, float(i), b0h));
-    }
-    const float u = fmaxf(r.rem - x.t[15], 0.f);
-    const float g = x.e[15] * (u * u * u);
-    if (g != 0.f) atomicAdd(h ? r.row + at.s[0] : base + 15, g * (h ? b0 : fmaf(b1, 15.f, b0)));
-  } else {
-#pragma unroll
-    for (int i = 0; i < 16; i++) {
-      const int j = (i + h) & 15;
-      int xx = at.s[0] + j;
-      if (xx >= QX) xx -= QX;
-      const float u = fmaxf(r.rem - x.t[i], 0.f);
-      const float g = x.e[i] * (u * u * u);
-      if (g != 0.f) atomicAdd(r.row + xx, g * fmaf(b1, float(j), b0));
-    }
-  }
-}
-
-// All nonlocal items of the CTA: warp w takes a contiguous range of items, so it mostly stays
-// on one atom and loads that atom's x factors once.
-template <int QX, int QY, int QZ, bool PROJ>
-__device__ __forceinline__ void nl_phase(const FusedAtomRec* atoms, const int* item_off, int na, const float* xfac,
-                                         const float* tabs, float inv_rc2, float hx, float* buf, int pitch,
-                                         float (*pacc)[4]) {
+template <bool PROJ>
+__device__ __forceinline__ void nl_phase(const FusedAtomRec* atoms, const int* pt_off, int na, long long rbase,
+                                         const float* __restrict__ lg, const unsigned* __restrict__ lw,
+                                         const float h[3], float* buf, float (*pacc)[4]) {
+  constexpr int U = 8;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_items = item_off[na];
-  const int it0 = (n_items * warp) / kFusedWarps, it1 = (n_items * (warp + 1)) / kFusedWarps;
-  int ai = 0, cur = -1;
-  NlAtom x;
-  for (int it = it0; it < it1; it++) {
-    while (item_off[ai + 1] <= it) ai++;
-    if (ai != cur) {
-      nl_atom(xfac + ai * 32, x);
-      cur = ai;
+  const int P = pt_off[na];
+  const int p0 = int((long long)P * warp / kFusedWarps), p1 = int((long long)P * (warp + 1) / kFusedWarps);
+  int a = 0;
+  while (a < na && pt_off[a + 1] <= p0) a++;
+  int pos = p0;
+  while (pos < p1 && a < na) {
+    const int seg_end = min(p1, pt_off[a + 1]);
+    const FusedAtomRec& at = atoms[a];
+    const long long eb = rbase + (long long)a * kProjCap - pt_off[a];
+    const float* c = pacc[a];
+    const float B0 = c[0] + c[1] * at.d0[0] + c[2] * at.d0[1] + c[3] * at.d0[2];
+    const float Bx = c[1] * h[0], By = c[2] * h[1], Bz = c[3] * h[2];
+    float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f;
+    for (int pb = pos + lane; pb < seg_end; pb += 32 * U) {
+      float g[U];
+      unsigned w[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int p = pb + 32 * u;
+        if (p < seg_end) {
+          g[u] = __ldg(lg + eb + p);
+          w[u] = __ldg(lw + eb + p);
+        } else {
+          g[u] = 0.f;
+          w[u] = 0u;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const float fx = small_float((w[u] >> 16) & 15u), fy = small_float((w[u] >> 20) & 15u),
+                    fz = small_float((w[u] >> 24) & 15u);
+        if (PROJ) {
+          const float gy = g[u] * buf[w[u] & 0xFFFFu];
+          S0 += gy;
+          S1 = fmaf(gy, fx, S1);
+          S2 = fmaf(gy, fy, S2);
+          S3 = fmaf(gy, fz, S3);
+        } else if (g[u] != 0.f) {
+          atomicAdd(buf + (w[u] & 0xFFFFu), g[u] * fmaf(Bx, fx, fmaf(By, fy, fmaf(Bz, fz, B0))));
+        }
+      }
     }
-    const FusedAtomRec& at = atoms[ai];
-    NlRow r;
-    nl_row<QY, QZ>(at, it - item_off[ai], tabs, inv_rc2, buf, pitch, r);
-    const float dx0 = tabs[at.toff];   // box displacements are affine: dx_j = dx0 + j hx
     if (PROJ) {
-      float acc[4];
-      nl_proj<QX>(at, x, r, dx0, hx, acc);
-      if (lane < 4) atomicAdd(&pacc[ai][lane], lane == 0 ? acc[0] : lane == 1 ? acc[1] : lane == 2 ? acc[2] : acc[3]);
-    } else {
-      nl_apply<QX>(at, x, r, dx0, hx, pacc[ai]);
+      for (int o = 16; o > 0; o >>= 1) {
+        S0 += __shfl_xor_sync(0xffffffffu, S0, o);
+        S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+        S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+        S3 += __shfl_xor_sync(0xffffffffu, S3, o);
+      }
+      // sum g y, sum g y dx, sum g y dy, sum g y dz (the coefficients are applied after the phase)
+      if (lane < 4)
+        atomicAdd(&pacc[a][lane], lane == 0 ? S0
+                                            : lane == 1 ? fmaf(at.d0[0], S0, h[0] * S1)
+                                                        : lane == 2 ? fmaf(at.d0[1], S0, h[1] * S2)
+                                                                    : fmaf(at.d0[2], S0, h[2] * S3));
     }
+    pos = seg_end;
+    a++;
   }
 }
 
@@ -315,22 +224,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   extern __shared__ __align__(16) unsigned char smem[];
   cf* S = reinterpret_cast<cf*>(smem);                               // [QZ][QY][HX]
   float* Sf = reinterpret_cast<float*>(smem);
-  float* tabs = reinterpret_cast<float*>(smem + HX * QY * QZ * 8);   // displacement tables
   __shared__ FusedAtomRec atoms[kFusedMaxAtoms];
   __shared__ float pacc[kFusedMaxAtoms][4];
   __shared__ float kmul[3][kMaxLine];
-  __shared__ int item_off[kFusedMaxAtoms + 1];   // nonlocal work items (atom, z-slice pair), atom-major
+  __shared__ int pt_off[kFusedMaxAtoms + 1];   // first point of each atom in the element's lists (atom-major)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int na = a.npa > 0 ? d.pa_count : 0;
 
-  // ---- prologue: atom records and tables (cooperative copies), multiplier tables ----
+  // ---- prologue: atom records and list lengths (cooperative copies), multiplier tables ----
   {
     const int* src = reinterpret_cast<const int*>(a.fatoms + d.pa_begin);
     int* dst = reinterpret_cast<int*>(atoms);
     constexpr int W = sizeof(FusedAtomRec) / 4;
     for (int i = threadIdx.x; i < na * W; i += blockDim.x) dst[i] = __ldg(src + i);
-    if (na > 0)
-      for (int i = threadIdx.x; i < d.tab_len; i += blockDim.x) tabs[i] = __ldg(a.dtab32 + d.tab_off + i);
+    for (int i = threadIdx.x; i < na; i += blockDim.x) pt_off[i + 1] = __ldg(a.plist.n + d.pa_begin + i);
     for (int i = threadIdx.x; i < 3 * kMaxLine; i += blockDim.x) {
       const int ax = i / kMaxLine, kk = i % kMaxLine;
       const int n = ax == 0 ? QX : (ax == 1 ? QY : QZ);
@@ -340,20 +247,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     for (int i = threadIdx.x; i < kFusedMaxAtoms * 4; i += blockDim.x) (&pacc[0][0])[i] = 0.f;
   }
   __syncthreads();
-  float* xfac = tabs + d.tab_len;   // [na][32]: e_x (0 beyond the box), then t_x (1e30 beyond the box)
-  for (int i = threadIdx.x; i < na * 32; i += blockDim.x) {
-    const int ai = i >> 5, j = i & 31, ix = j & 15;
-    const FusedAtomRec& at = atoms[ai];
-    const float dx = tabs[at.toff] + float(ix) * float(d.h[0]);
-    const bool in = ix < at.l[0];
-    xfac[i] = j < 16 ? (in ? __expf(-dx * dx * at.inv2s2) : 0.f) : (in ? dx * dx * a.inv_rc2 : 1e30f);
-  }
   if (threadIdx.x == 0) {
-    item_off[0] = 0;
-    for (int ai = 0; ai < na; ai++) item_off[ai + 1] = item_off[ai] + (atoms[ai].l[2] + 1) / 2;
+    pt_off[0] = 0;
+    for (int ai = 0; ai < na; ai++) pt_off[ai + 1] += pt_off[ai];
   }
-  const float inv_rc2 = a.inv_rc2;
-  const float hx = float(d.h[0]);
+  const float hh[3] = {float(d.h[0]), float(d.h[1]), float(d.h[2])};
+  const long long lbase = (long long)d.pa_begin * kProjCap;
   const long long vbase = a.xo[k] + (long long)v * (QX * QY * QZ);
   const float4* y4 = reinterpret_cast<const float4*>(Y + vbase);
 
@@ -382,7 +281,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   }
   __syncthreads();
   // ---- phase 1b: projector overlaps <b, y> from the real rows ----
-  nl_phase<QX, QY, QZ, true>(atoms, item_off, na, xfac, tabs, inv_rc2, hx, Sf, PITCH, pacc);
+  nl_phase<true>(atoms, pt_off, na, lbase, a.plist.g, a.plist.w, hh, Sf, pacc);
   __syncthreads();
   // ---- phase 1c: R2C along x in each row slot: z = x_even + i x_odd, X_k = E_k + w^k O_k ----
   for (int r = threadIdx.x; r < NROW; r += blockDim.x) {
@@ -482,7 +381,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   }
   __syncthreads();
   // ---- phase 5b: nonlocal application ((atom, z-slice pair) items, shared atomics) ----
-  nl_phase<QX, QY, QZ, false>(atoms, item_off, na, xfac, tabs, inv_rc2, hx, Sf, PITCH, pacc);
+  nl_phase<false>(atoms, pt_off, na, lbase, a.plist.g, a.plist.w, hh, Sf, pacc);
   __syncthreads();
   // ---- phase 5c: V y, Chebyshev combination, store (coalesced float4) ----
   float alpha = 1.f, shift = 0.f, beta = 0.f;
@@ -555,17 +454,76 @@ int set_fused_smem_limits() {
   return e;
 }
 
-// Displacement-table capacity (floats) of the fused instance for this Q shape; 0 = no instance.
-int fused_tab_capacity(const int qn[3]) {
-#define DGDFT_CAP(a, b, c) \
-  if (qn[0] == a && qn[1] == b && qn[2] == c) return fused_tab_floats<a, b, c>();
-  DGDFT_FUSED_SHAPES(DGDFT_CAP)
-#undef DGDFT_CAP
+// 1 when the fused kernel is instantiated for this Q shape.
+int fused_shape_supported(const int qn[3]) {
+#define DGDFT_HAS(a, b, c) \
+  if (qn[0] == a && qn[1] == b && qn[2] == c) return 1;
+  DGDFT_FUSED_SHAPES(DGDFT_HAS)
+#undef DGDFT_HAS
   return 0;
 }
 
-// 1 when the fused kernel is instantiated for this Q shape.
-int fused_shape_supported(const int qn[3]) { return fused_tab_capacity(qn) > 0; }
+// ---- the compact projector-point lists of every fused atom record (once per plan) ----
+// One CTA of 256 threads per record: thread t examines the box points 16t .. 16t+15 in (z, y, x) order,
+// a block-wide prefix sum places the points inside the support ball without changing their order.
+__global__ void __launch_bounds__(256) k_build_proj_lists(const FusedAtomRec* fat, const double* dtab, int n,
+                                                          double inv_rc2, ProjList pl) {
+  const int r = blockIdx.x;
+  if (r >= n) return;
+  const FusedAtomRec at = fat[r];
+  __shared__ int scan[256];
+  const double* t = dtab + at.dtab;
+  const int pitch = 2 * (at.qn[0] / 2 + 1);
+  float gv[16];
+  unsigned wv[16];
+  int local = 0;
+#pragma unroll
+  for (int q = 0; q < 16; q++) {
+    const int e = threadIdx.x * 16 + q;
+    const int iz = e >> 8, iy = (e >> 4) & 15, ix = e & 15;
+    gv[q] = 0.f;
+    wv[q] = 0u;
+    if (ix < at.l[0] && iy < at.l[1] && iz < at.l[2]) {
+      const double dx = t[ix], dy = t[at.l[0] + iy], dz = t[at.l[0] + at.l[1] + iz];
+      const double d2 = dx * dx + dy * dy + dz * dz;
+      const double u = 1.0 - d2 * inv_rc2;
+      if (u > 0.0) {
+        gv[q] = float(exp(-d2 * double(at.inv2s2)) * u * u * u);
+        int xx = at.s[0] + ix; if (xx >= at.qn[0]) xx -= at.qn[0];
+        int yy = at.s[1] + iy; if (yy >= at.qn[1]) yy -= at.qn[1];
+        int zz = at.s[2] + iz; if (zz >= at.qn[2]) zz -= at.qn[2];
+        wv[q] = unsigned((zz * at.qn[1] + yy) * pitch + xx) | (unsigned(ix) << 16) | (unsigned(iy) << 20) |
+                (unsigned(iz) << 24);
+        local++;
+      }
+    }
+  }
+  scan[threadIdx.x] = local;
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    const int v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
+    __syncthreads();
+    scan[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int pos = scan[threadIdx.x] - local;
+  const long long base = (long long)r * kProjCap;
+#pragma unroll
+  for (int q = 0; q < 16; q++)
+    if (gv[q] != 0.f) {
+      pl.g[base + pos] = gv[q];
+      pl.w[base + pos] = wv[q];
+      pos++;
+    }
+  if (threadIdx.x == 255) pl.n[r] = scan[255];
+}
+
+void launch_build_proj_lists(const FusedAtomRec* fat, const double* dtab, int n, double r_cut, ProjList pl,
+                             cudaStream_t st) {
+  if (n <= 0) return;
+  count_launch();
+  k_build_proj_lists<<<n, 256, 0, st>>>(fat, dtab, n, 1.0 / (r_cut * r_cut), pl);
+}
 
 // Returns 1 when the fused kernel handled the group (FP32, supported shape, fits shared memory).
 int launch_fused_group(const ShapeGroup& g, const HxArgs& h, const float* X, float* Y, const float* Yprev,
@@ -575,11 +533,10 @@ int launch_fused_group(const ShapeGroup& g, const HxArgs& h, const float* X, flo
   a.elems = nullptr;
   a.flags = h.flags;
   a.fatoms = h.fatoms;
-  a.dtab32 = h.dtab32;
+  a.plist = h.plist;
   a.xo = h.xo;
   a.nvec_mode = h.nvec_mode;
   a.npa = h.n_proj_per_atom;
-  a.inv_rc2 = float(1.0 / (h.r_cut * h.r_cut));
   int done = 0;
 #define DGDFT_LAUNCH(qx, qy, qz) \
   done = done || launch_shape<qx, qy, qz>(g, a, X, Y, Yprev, V, cheb, cheb_stride, out_mode, st);

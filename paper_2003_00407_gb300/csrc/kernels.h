@@ -32,8 +32,8 @@ struct HxArgs {
   int nvec_mode;
   int n_proj_per_atom;
   double r_cut;
-  const FusedAtomRec* fatoms;  // FP32 atom records (fused kernel)
-  const float* dtab32;
+  const FusedAtomRec* fatoms;  // atom records of the fused kernel
+  ProjList plist;              // their compact projector-point lists
 };
 
 struct ShapeGroup {
@@ -53,7 +53,9 @@ struct HxPlan {
 
 int fused_shape_supported(const int qn[3]);
 int set_fused_smem_limits();   // per device; returns the cudaError_t
-int fused_tab_capacity(const int qn[3]);
+// compact projector-point lists of the fused atom records (k_fused.cu), once per plan
+void launch_build_proj_lists(const FusedAtomRec* fat, const double* dtab, int n, double r_cut, ProjList pl,
+                             cudaStream_t st);
 // fused FP32 Chebyshev step (k_fused.cu): returns 1 when it handled the group
 int launch_fused_group(const ShapeGroup& g, const HxArgs& h, const float* X, float* Y, const float* Yprev,
                        const float* V, const double* cheb, int cheb_stride, int out_mode, cudaStream_t st);

@@ -102,8 +102,11 @@ extern "C" int dgdft_apply_hamiltonian_noalloc(const dgdft_problem* prob, const 
   const size_t o_desc = b.take(P.desc.size() * sizeof(ElemDesc));
   const size_t o_boxes = b.take(std::max<size_t>(1, P.boxes.size()) * sizeof(AtomBox));
   const size_t o_dtab = b.take(P.dtab.size() * sizeof(double));
-  const size_t o_dtab32 = b.take(P.dtab32.size() * sizeof(float));
   const size_t o_fat = b.take(std::max<size_t>(1, P.fatoms.size()) * sizeof(FusedAtomRec));
+  const size_t nq = size_t(std::max(1, P.n_qboxes));
+  const size_t o_plg = b.take(nq * kProjCap * sizeof(float));
+  const size_t o_plw = b.take(nq * kProjCap * sizeof(unsigned));
+  const size_t o_pln = b.take(nq * sizeof(int));
   const size_t o_xoff = b.take(P.off[OFF_X].size() * sizeof(long long));
   std::vector<size_t> o_grp(P.hx.groups.size());
   for (size_t i = 0; i < P.hx.groups.size(); i++) o_grp[i] = b.take(P.hx.groups[i].elems.size() * sizeof(int));
@@ -123,7 +126,6 @@ extern "C" int dgdft_apply_hamiltonian_noalloc(const dgdft_problem* prob, const 
   bool ok = up(o_desc, P.desc.data(), P.desc.size() * sizeof(ElemDesc)) &&
             up(o_boxes, P.boxes.data(), P.boxes.size() * sizeof(AtomBox)) &&
             up(o_dtab, P.dtab.data(), P.dtab.size() * sizeof(double)) &&
-            up(o_dtab32, P.dtab32.data(), P.dtab32.size() * sizeof(float)) &&
             up(o_fat, P.fatoms.data(), P.fatoms.size() * sizeof(FusedAtomRec)) &&
             up(o_xoff, P.off[OFF_X].data(), P.off[OFF_X].size() * sizeof(long long));
   for (size_t i = 0; ok && i < P.hx.groups.size(); i++) {
@@ -158,7 +160,9 @@ extern "C" int dgdft_apply_hamiltonian_noalloc(const dgdft_problem* prob, const 
   h.n_proj_per_atom = P.n_proj_per_atom;
   h.r_cut = P.r_cut;
   h.fatoms = reinterpret_cast<const FusedAtomRec*>(base + o_fat);
-  h.dtab32 = reinterpret_cast<const float*>(base + o_dtab32);
+  h.plist = ProjList{reinterpret_cast<float*>(base + o_plg), reinterpret_cast<unsigned*>(base + o_plw),
+                     reinterpret_cast<int*>(base + o_pln)};
+  if (P.n_qboxes > 0) launch_build_proj_lists(h.fatoms, h.dtab, P.n_qboxes, P.r_cut, h.plist, st);
   for (const ShapeGroup& g : P.hx.groups)
     if (!launch_fused_group(g, h, X, Y, nullptr, V32, nullptr, 0, OUT_APPLY, st))
       return fail(nullptr, DGDFT_UNSUPPORTED, "noalloc: fused kernel unavailable for a Q shape");

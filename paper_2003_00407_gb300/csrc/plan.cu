@@ -202,7 +202,7 @@ int build_plan(const dgdft_problem* pr, const dgdft_alb_params* prm, Plan& P, st
     d.n_proj_e = ncol;
   }
   if (P.dtab.empty()) P.dtab.push_back(0.0);
-  P.dtab32.assign(P.dtab.begin(), P.dtab.end());
+  P.n_qboxes = M > 0 ? P.desc[0].pe_begin : 0;
   P.fatoms.assign(P.boxes.size(), FusedAtomRec{});
   for (int k = 0; k < M; k++) {
     ElemDesc& d = P.desc[k];
@@ -211,13 +211,16 @@ int build_plan(const dgdft_problem* pr, const dgdft_alb_params* prm, Plan& P, st
     for (int i = 0; i < d.pa_count; i++) {
       const AtomBox& b = P.boxes[d.pa_begin + i];
       FusedAtomRec& r = P.fatoms[d.pa_begin + i];
-      for (int q = 0; q < 3; q++) { r.s[q] = b.s[q]; r.l[q] = b.l[q]; }
-      r.toff = b.toff - d.tab_off;
+      for (int q = 0; q < 3; q++) { r.s[q] = b.s[q]; r.l[q] = b.l[q]; r.qn[q] = d.qn[q]; }
+      r.dtab = b.toff;
+      r.d0[0] = float(P.dtab[b.toff]);
+      r.d0[1] = float(P.dtab[b.toff + b.l[0]]);
+      r.d0[2] = float(P.dtab[b.toff + b.l[0] + b.l[1]]);
       r.inv2s2 = float(0.5 / (b.pwidth * b.pwidth));
       const int npa = pr->n_proj_per_atom;
       r.c[0] = npa >= 1 ? float(b.gamma[0] * b.ns * b.ns * d.dV) : 0.f;
       for (int q = 1; q < 4; q++) r.c[q] = npa == 4 ? float(b.gamma[q] * b.np * b.np * d.dV) : 0.f;
-      d.tab_len = std::max(d.tab_len, r.toff + b.l[0] + b.l[1] + b.l[2]);
+      d.tab_len = std::max(d.tab_len, b.toff - d.tab_off + b.l[0] + b.l[1] + b.l[2]);
     }
     for (int a = 0; a < 3; a++) {
       const double g = 2.0 * M_PI / (d.qn[a] * d.h[a]);
@@ -291,10 +294,10 @@ int build_plan(const dgdft_problem* pr, const dgdft_alb_params* prm, Plan& P, st
     }
     ShapeGroup& g = P.hx.groups[it->second];
     if (g.elems.empty()) g.fused_ok = true;
-    if (d.pa_count > kFusedAtomLimit || d.tab_len + 32 * d.pa_count > fused_tab_capacity(d.qn)) g.fused_ok = false;
+    if (d.pa_count > kFusedAtomLimit) g.fused_ok = false;
     for (int ai = 0; ai < d.pa_count; ai++)
       for (int q = 0; q < 3; q++)
-        if (P.boxes[d.pa_begin + ai].l[q] > 16) g.fused_ok = false;   // boxes must fit the 16^3 tables
+        if (P.boxes[d.pa_begin + ai].l[q] > 16) g.fused_ok = false;   // boxes must fit the 16^3 list slots
     g.elems.push_back(k);
     g.n_elems = int(g.elems.size());
     g.max_nblk = std::max(g.max_nblk, d.n_blk);

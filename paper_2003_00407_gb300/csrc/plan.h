@@ -18,7 +18,6 @@ struct Plan {
   std::vector<ElemDesc> desc;
   std::vector<AtomBox> boxes;   // Q boxes of all elements, then E boxes
   std::vector<double> dtab;
-  std::vector<float> dtab32;          // FP32 copy of dtab (fused kernel)
   std::vector<FusedAtomRec> fatoms;   // parallel to boxes (Q boxes filled)
   HxPlan hx;
   std::vector<long long> off[kOffKinds];
@@ -32,7 +31,8 @@ struct Plan {
   ElemDesc* d_desc = nullptr;
   AtomBox* d_boxes = nullptr;
   double* d_dtab = nullptr;
-  float* d_dtab32 = nullptr;
+  ProjList plist{nullptr, nullptr, nullptr};   // compact projector-point lists of the Q boxes (device)
+  int n_qboxes = 0;                            // the Q boxes come first in `boxes`
   FusedAtomRec* d_fatoms = nullptr;
   long long* d_off[kOffKinds] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };

@@ -1,6 +1,6 @@
 """Parity of the slab (8x8 elements), the uneven batch (256 elements of 18 grid shapes) and the
 band-energy gradient (8x8 elements, kT 0.01 Ha) at their full sizes, mixed precision, Chebyshev
-degree 80, tol 1e-8 (the benchmark's launch configuration), against oracle values stored by
+degree 100, tol 1e-8 (the benchmark's launch configuration), against oracle values stored by
 tests/golden/make_c2_c4.py and tests/golden/make_c3_samples.py, plus one slab element solved live.
 
 Bounds as in test_gpu_fullsize: eigenvalues 1e-6 Ha; singular values of the restricted block 1e-5
@@ -35,7 +35,7 @@ def ctx():
 def _run(ctx, w, dg=True):
     from paper_2003_00407_gb300 import api, _abi
     p, q = w.problem, w.params
-    res = api.alb_generate(ctx, p, q, precision=_abi.MIXED, cheb_degree=80, tol=1e-8, max_iter=60,
+    res = api.alb_generate(ctx, p, q, precision=_abi.MIXED, cheb_degree=100, tol=1e-8, max_iter=60,
                            keep_eigvec=True)
     blocks = api.dg_assemble(ctx, p, q, res, w.alpha).cpu().numpy() if dg else None
     st = res.status.cpu().numpy()

@@ -69,7 +69,7 @@ def _c2(ctx, precision):
         if precision == 0:
             res = api.alb_generate(ctx, p, q, precision=0, cheb_degree=40, tol=1e-10, max_iter=200)
         else:
-            res = api.alb_generate(ctx, p, q, precision=1, cheb_degree=80, tol=1e-8, max_iter=60)
+            res = api.alb_generate(ctx, p, q, precision=1, cheb_degree=100, tol=1e-8, max_iter=60)
         st = res.status.cpu().numpy()
         assert np.count_nonzero(st) == 0, np.nonzero(st)
         _C2[precision] = (w, res, api.dg_assemble(ctx, p, q, res, w.alpha))
@@ -152,7 +152,7 @@ def test_uneven_multipass_shape_live_subspace(ctx):
         ws = subset(w, [k])
         ws.problem.n_stencil = 1
         ws.problem.neighbors = np.zeros((1, 1), dtype=np.int32)
-        res = api.alb_generate(ctx, ws.problem, ws.params, precision=1, cheb_degree=80, tol=1e-8, max_iter=60)
+        res = api.alb_generate(ctx, ws.problem, ws.params, precision=1, cheb_degree=100, tol=1e-8, max_iter=60)
         o = live.get(timeout=3600)
     finally:
         pool.terminate()

@@ -1,5 +1,5 @@
 """Full-size parity on the 1024-element sheet (32x32 elements of 32x32x48, 4096 atoms) in the
-launch configuration the benchmark times: mixed precision, Chebyshev degree 80, tol 1e-8.
+launch configuration the benchmark times: mixed precision, Chebyshev degree 100, tol 1e-8.
 
 Sampled elements are compared with oracle values stored by tests/golden/make_c5_samples.py
 (eigenvalues, singular values of the restricted block, eigenvalues of the diagonal DG block), and
@@ -44,7 +44,7 @@ def test_sheet_1024_elements_sampled(ctx):
     pool = mp.get_context("spawn").Pool(len(LIVE))
     live = {k: pool.apply_async(helpers.oracle_element, (5, k, 40, 1e-10, 100, w.alpha)) for k in LIVE}
     try:
-        res = api.alb_generate(ctx, p, q, precision=_abi.MIXED, cheb_degree=80, tol=1e-8, max_iter=60,
+        res = api.alb_generate(ctx, p, q, precision=_abi.MIXED, cheb_degree=100, tol=1e-8, max_iter=60,
                                keep_eigvec=False)
         blocks = api.dg_assemble(ctx, p, q, res, w.alpha).cpu().numpy()
         ev = res.eigval.cpu().numpy()
