@@ -20,6 +20,8 @@ It is a plain, slow, obviously correct NumPy/SciPy restatement of the method
 * ``dg_solve``       -- eigenpairs of the assembled DG Hamiltonian (Eq.
   DGEigenvalue) by CheFSI applied block by block, and the DG electron density
   (the next steps of the method).
+* ``lobpcg``         -- LOBPCG with the Teter preconditioner (Alg. LOBPCG, Eqs. 3-5), the
+  paper's default local solver, as a second route to the same eigenpairs.
 * ``driver``         -- all of the above over every element of a workload.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
@@ -27,4 +29,4 @@ brute force and finite differences.  Parity unpinned: the Chebyshev filter's
 bound heuristics (Lanczos step count, lower bound from the largest Ritz
 value) only change iteration counts, not the converged result.
 """
-from . import local_operator, chefsi, alb, dg, grad, driver, dg_solve  # noqa: F401
+from . import local_operator, chefsi, alb, dg, grad, driver, dg_solve, lobpcg  # noqa: F401
