@@ -65,6 +65,12 @@ enum dgdft_precision {
                       then one FP64 Rayleigh-Ritz sweep */
 };
 
+enum dgdft_solver {
+  DGDFT_CHEFSI = 0,  /* Chebyshev-filtered subspace iteration (Alg. CheFSI), both precisions */
+  DGDFT_LOBPCG = 1   /* LOBPCG with the Teter preconditioner (Alg. LOBPCG, Eqs. 3-5): DGDFT_FP64, the
+                        same n_blk <= 32 in every element (the projected problem has 3 n_blk <= 96) */
+};
+
 enum dgdft_flags {
   DGDFT_HOST_BUFFERS = 1  /* data arrays are host memory (see Conventions) */
 };
@@ -120,6 +126,7 @@ typedef struct {
                                 iterations of Sec. III).  Its n_eig vectors replace the first n_eig of
                                 the start block (FP32-rounded in DGDFT_MIXED); the guard vectors keep
                                 the SplitMix64 start.  Need not be orthonormal (CholQR2 follows). */
+  int solver;                /* dgdft_solver (0 = CheFSI); cheb_degree and lanczos_steps apply to CheFSI */
 } dgdft_alb_params;
 
 /* Results of dgdft_alb_generate (DATA arrays; caller allocated).  Sizes in

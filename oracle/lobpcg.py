@@ -5,7 +5,8 @@ The paper's default plane-wave eigensolver for small local problems.  Per iterat
 order:
 
 1. W = T R with R = H X - X (X^T H X) dV (Eq. 3), T the Teter preconditioner (below);
-2. trial subspace S = [X, W, P] (P absent in the first iteration);
+2. trial subspace S = [X, W, P] (P absent in the first iteration); the rows of W and P are scaled to unit
+   norm first, which leaves the subspace unchanged and keeps S^T S well conditioned as R -> 0;
 3. the projected generalized problem S^T H S C = S^T S C Lambda (Eq. 5), lowest n_blk pairs;
 4. P = W C_W + P C_P (the conjugate direction), X = X C_X + P (Eq. 4).
 
@@ -68,6 +69,7 @@ def lobpcg(op, n_eig, n_blk, tol, max_iter, X0):
         if resid[:n_eig].max() <= tol or it >= max_iter:
             break
         W = teter_precondition(op, R, kinetic_energy(op, X))
+        W = W / np.sqrt((W * W).sum(axis=1) * dV)[:, None]   # unit rows: same span, better-conditioned S^T S
         HW = op.apply(W)
         parts = [X, W] + ([P] if P is not None else [])
         hparts = [HX, HW] + ([HP] if HP is not None else [])
@@ -85,7 +87,8 @@ def lobpcg(op, n_eig, n_blk, tol, max_iter, X0):
         HP_new = CW.T @ HW + (CP.T @ HP if P is not None else 0.0)
         X = CX.T @ X + P_new                   # Eq. 4
         HX = CX.T @ HX + HP_new
-        P, HP = P_new, HP_new
+        pn = np.sqrt((P_new * P_new).sum(axis=1) * dV)[:, None]
+        P, HP = P_new / pn, HP_new / pn        # unit rows for the next trial subspace (same span)
         theta = lam[:n_blk]
         it += 1
     return dict(theta=theta, X=X, resid=resid, iters=it, converged=bool(resid[:n_eig].max() <= tol),

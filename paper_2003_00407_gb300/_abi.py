@@ -11,6 +11,7 @@ OK, INVALID_ARG, OUT_OF_MEMORY, NOT_CONVERGED, CHOLESKY_FAIL, BAD_INPUT, TIMEOUT
 STATUS_NAMES = ["OK", "INVALID_ARG", "OUT_OF_MEMORY", "NOT_CONVERGED", "CHOLESKY_FAIL", "BAD_INPUT", "TIMEOUT",
                 "CUDA_ERROR", "UNSUPPORTED"]
 FP64, MIXED = 0, 1
+CHEFSI, LOBPCG = 0, 1
 HOST_BUFFERS = 1
 
 PI = C.POINTER(C.c_int)
@@ -29,7 +30,8 @@ class Problem(C.Structure):
 class AlbParams(C.Structure):
     _fields_ = [("n_eig", PI), ("n_alb", PI), ("n_blk", PI), ("cheb_degree", C.c_int), ("tol", C.c_double),
                 ("tol_mixed", C.c_double), ("max_iter", C.c_int), ("lanczos_steps", C.c_int),
-                ("precision", C.c_int), ("seed", C.c_uint64), ("flags", C.c_int), ("x0", C.c_void_p)]
+                ("precision", C.c_int), ("seed", C.c_uint64), ("flags", C.c_int), ("x0", C.c_void_p),
+                ("solver", C.c_int)]
 
 
 class AlbResult(C.Structure):

@@ -38,7 +38,7 @@ class Marshalled:
     """Keeps the numpy buffers alive while the C structures point into them."""
 
     def __init__(self, prob, params, *, precision, cheb_degree, tol, max_iter, tol_mixed=0.0,
-                 lanczos_steps=10, seed=None, flags=0, v_extra=None, x0=None):
+                 lanczos_steps=10, seed=None, flags=0, v_extra=None, x0=None, solver=0):
         self.keep = []
 
         def keep(a):
@@ -82,6 +82,7 @@ class Marshalled:
         q.seed = int(params.seed if seed is None else seed)
         q.flags = int(flags)
         q.x0 = C.c_void_p(0 if x0 is None else x0)
+        q.solver = int(solver)
         self.params = q
 
 
@@ -156,7 +157,7 @@ def v_extra_tensor(prob, device="cuda"):
 
 def alb_generate(ctx: Context, prob, params, *, precision=_abi.FP64, cheb_degree=None, tol=None, max_iter=None,
                  tol_mixed=0.0, keep_eigvec=True, v_extra=None, allow_not_converged=True, host_buffers=False,
-                 x0=None):
+                 x0=None, solver=_abi.CHEFSI):
     """ALB generation for every element (dgdft_alb_generate).  Returns ALBResult of device tensors.
 
     x0: optional warm start, a float64 tensor in the packed [n_eig][N] layout of ALBResult.eigvec (on the
@@ -171,7 +172,7 @@ def alb_generate(ctx: Context, prob, params, *, precision=_abi.FP64, cheb_degree
                    max_iter=params.max_iter if max_iter is None else max_iter, tol_mixed=tol_mixed,
                    flags=_abi.HOST_BUFFERS if host_buffers else 0,
                    v_extra=None if v_extra is None else v_extra.data_ptr(),
-                   x0=None if x0 is None else x0.data_ptr())
+                   x0=None if x0 is None else x0.data_ptr(), solver=solver)
     m.keep.append(v_extra)
     if x0 is not None:
         if x0.dtype != torch.float64 or not x0.is_contiguous():

@@ -354,6 +354,143 @@ int chefsi_stage(dgdft_ctx* ctx, Plan& P, const Common& c, Stage<T>& s, const dg
   return DGDFT_OK;
 }
 
+// LOBPCG local solver with the Teter preconditioner (Alg. LOBPCG, Eqs. 3-5), FP64, the same block size n
+// (<= 32) in every element.  On entry X holds the random start; on exit X holds the Ritz vectors, c.theta /
+// c.resid the Ritz values and residuals (ld P.L) and c.iters the iteration count.  The projected problem
+// over [X, W, P] (3n <= 96) is solved by the generalised Rayleigh-Ritz kernel of the CheFSI path.
+int lobpcg_stage(dgdft_ctx* ctx, Plan& P, const Common& c, const dgdft_alb_params* prm, double* X,
+                 cudaStream_t st, double* history, double** x_out) {
+  if (history)
+    for (int i = 0; i < prm->max_iter + 2; i++) history[i] = -1.0;
+  const int M = P.M, n = P.desc.empty() ? 0 : P.desc[0].n_blk;
+  const int L3 = 3 * P.L;
+  const size_t blk = size_t(P.tot[OFF_X]) * sizeof(double);
+  double *HX, *W, *HW, *Pd, *HP, *Xn, *HXn, *Pn, *HPn, *TX, *C3, *G3, *A3, *th3, *r3, *rs3, *ek;
+  cplx<double>* S;
+  WS(HX, "lob_HX", blk);
+  WS(W, "lob_W", blk);
+  WS(HW, "lob_HW", blk);
+  WS(Pd, "lob_P", blk);
+  WS(HP, "lob_HP", blk);
+  WS(Xn, "lob_Xn", blk);
+  WS(HXn, "lob_HXn", blk);
+  WS(Pn, "lob_Pn", blk);
+  WS(HPn, "lob_HPn", blk);
+  WS(TX, "lob_TX", blk);
+  WS(S, "S_spec", size_t(P.tot[OFF_S]) * sizeof(cplx<double>));
+  WS(C3, "lob_C3", size_t(M) * L3 * L3 * sizeof(double));
+  WS(G3, "lob_G3", size_t(M) * L3 * L3 * sizeof(double));
+  WS(A3, "lob_A3", size_t(M) * L3 * L3 * sizeof(double));
+  WS(th3, "lob_theta", size_t(M) * L3 * sizeof(double));
+  WS(r3, "lob_resid2", size_t(M) * L3 * sizeof(double));
+  WS(rs3, "lob_resid", size_t(M) * L3 * sizeof(double));
+  WS(ek, "lob_ekin", size_t(M) * L3 * sizeof(double));
+  // element descriptors with the trial-subspace sizes 2n and 3n for the projected problem
+  ElemDesc *d2, *d3;
+  WS(d2, "lob_desc2", size_t(M) * sizeof(ElemDesc));
+  WS(d3, "lob_desc3", size_t(M) * sizeof(ElemDesc));
+  {
+    std::vector<ElemDesc> h2(P.desc), h3(P.desc);
+    for (int k = 0; k < M; k++) {
+      h2[k].n_blk = 2 * n;
+      h3[k].n_blk = 3 * n;
+    }
+    CUDA_OK(cudaMemcpyAsync(d2, h2.data(), M * sizeof(ElemDesc), cudaMemcpyHostToDevice, st));
+    CUDA_OK(cudaMemcpyAsync(d3, h3.data(), M * sizeof(ElemDesc), cudaMemcpyHostToDevice, st));
+    CUDA_OK(cudaStreamSynchronize(st));   // h2, h3 are host temporaries
+  }
+  BatchArgs b{P.d_desc, c.flags, M};
+  const long long* ox = P.d_off[OFF_X];
+  const size_t mat3 = size_t(M) * L3 * L3 * sizeof(double);
+  HxArgs ha = hx_args(P, c.flags, OFF_X, NV_BLK);
+  set_group_nvec(P, NV_BLK);
+  // start: CholQR2 and Rayleigh-Ritz of the random block
+  cholqr<double>(P, c, X, 1e-13, st);
+  cholqr<double>(P, c, X, 1e-13, st);
+  hx<double>(P, c, c.flags, OFF_X, NV_BLK, X, HX, nullptr, S, nullptr, 0, OUT_APPLY, st);
+  CUDA_OK(cudaMemsetAsync(G3, 0, mat3, st));
+  CUDA_OK(cudaMemsetAsync(A3, 0, mat3, st));
+  launch_gram<double>(b, X, ox, NV_BLK, X, ox, NV_BLK, 4, nullptr, nullptr, G3, L3, st);
+  launch_gram<double>(b, X, ox, NV_BLK, HX, ox, NV_BLK, 4, nullptr, nullptr, A3, L3, st);
+  launch_rr_small(b, G3, A3, C3, th3, L3, NV_BLK, c.flags, st);
+  launch_rotate<double, double>(b, X, ox, X, ox, NV_BLK, NV_BLK, 4, C3, L3, HX, HX, nullptr, nullptr, L3, st);
+  bool have_p = false;
+  for (int it = 0;; it++) {
+    // residuals R = HX - X theta (into W) and the convergence test
+    CUDA_OK(cudaMemsetAsync(r3, 0, size_t(M) * L3 * sizeof(double), st));
+    launch_lobpcg_resid(b, X, HX, ox, th3, L3, W, r3, st);
+    CUDA_OK(cudaMemsetAsync(c.active, 0, 4 * sizeof(int), st));
+    launch_update_convergence(b, r3, L3, rs3, th3, c.bounds, prm->tol, 0.0, 0, c.prevres, c.stall, c.flags,
+                              c.active, c.iters, st);
+    CUDA_OK(cudaMemcpyAsync(ctx->h_active, c.active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_OK(cudaStreamSynchronize(st));
+    if (history) {
+      double mx;
+      std::memcpy(&mx, ctx->h_active + 2, sizeof(double));
+      history[it] = mx;
+    }
+    if (*ctx->h_active == 0) break;
+    if (it == prm->max_iter) {
+      std::vector<int> hf(M), hc(M, 0);
+      CUDA_OK(cudaMemcpy(hf.data(), c.flags, M * sizeof(int), cudaMemcpyDeviceToHost));
+      for (int k = 0; k < M; k++) hc[k] = (hf[k] & EF_ACTIVE) ? 1 : 0;
+      CUDA_OK(cudaMemcpy(c.hitcap, hc.data(), M * sizeof(int), cudaMemcpyHostToDevice));
+      break;
+    }
+    // W = T R: Teter factor per band with E_v = <x_v, T x_v> dV (Eq. 3)
+    launch_forward<double>(P.hx, ha, X, S, st);
+    launch_zline<double>(P.hx, ha, S, MULT_KINETIC, st);
+    launch_inverse_raw<double>(P.hx, ha, S, TX, st);
+    CUDA_OK(cudaMemsetAsync(ek, 0, size_t(M) * L3 * sizeof(double), st));
+    launch_vec_dots(b, X, TX, ox, L3, ek, st);
+    HxArgs ht = ha;
+    ht.mref = ek;
+    ht.mref_ld = L3;
+    launch_forward<double>(P.hx, ht, W, S, st);
+    launch_zline<double>(P.hx, ht, S, MULT_TETER, st);
+    launch_inverse_raw<double>(P.hx, ht, S, W, st);
+    // unit rows of W (the span of the trial subspace is unchanged; S^T S stays well conditioned)
+    CUDA_OK(cudaMemsetAsync(ek, 0, size_t(M) * L3 * sizeof(double), st));
+    launch_vec_dots(b, W, W, ox, L3, ek, st);
+    launch_scale_rows(b, W, nullptr, ox, ek, L3, st);
+    hx<double>(P, c, c.flags, OFF_X, NV_BLK, W, HW, nullptr, S, nullptr, 0, OUT_APPLY, st);
+    // projected problem over S = [X, W(, P)] (Eq. 5): Gram and H blocks, generalised Rayleigh-Ritz
+    const int nb = have_p ? 3 : 2;
+    const double* Sb[3] = {X, W, Pd};
+    const double* Hb[3] = {HX, HW, HP};
+    CUDA_OK(cudaMemsetAsync(G3, 0, mat3, st));
+    CUDA_OK(cudaMemsetAsync(A3, 0, mat3, st));
+    for (int i = 0; i < nb; i++)
+      for (int j = 0; j < nb; j++) {
+        const size_t o = size_t(i) * n * L3 + size_t(j) * n;
+        launch_gram<double>(b, Sb[i], ox, NV_BLK, Sb[j], ox, NV_BLK, 4, nullptr, nullptr, G3 + o, L3, st);
+        launch_gram<double>(b, Sb[i], ox, NV_BLK, Hb[j], ox, NV_BLK, 4, nullptr, nullptr, A3 + o, L3, st);
+      }
+    BatchArgs bp{have_p ? d3 : d2, c.flags, M};
+    g_max_nblk = nb * n;
+    launch_rr_small(bp, G3, A3, C3, th3, L3, NV_BLK, c.flags, st);
+    g_max_nblk = n;
+    // X = X C_X + P', P' = W C_W + P C_P (Eq. 4) and their H-images
+    launch_lobpcg_update(b, ox, C3, L3, nb, X, W, Pd, HX, HW, HP, Xn, Pn, HXn, HPn, st);
+    CUDA_OK(cudaMemsetAsync(ek, 0, size_t(M) * L3 * sizeof(double), st));
+    launch_vec_dots(b, Pn, Pn, ox, L3, ek, st);
+    launch_scale_rows(b, Pn, HPn, ox, ek, L3, st);   // unit rows of the next conjugate block
+    std::swap(X, Xn);
+    std::swap(HX, HXn);
+    std::swap(Pd, Pn);
+    std::swap(HP, HPn);
+    have_p = true;
+  }
+  // Ritz values and residual norms in the result layout (ld P.L)
+  CUDA_OK(cudaMemcpy2DAsync(c.theta, P.L * sizeof(double), th3, L3 * sizeof(double), P.L * sizeof(double), M,
+                            cudaMemcpyDeviceToDevice, st));
+  CUDA_OK(cudaMemcpy2DAsync(c.resid, P.L * sizeof(double), rs3, L3 * sizeof(double), P.L * sizeof(double), M,
+                            cudaMemcpyDeviceToDevice, st));
+  CUDA_OK(cudaGetLastError());
+  *x_out = X;
+  return DGDFT_OK;
+}
+
 }  // namespace dgdft
 
 using namespace dgdft;
@@ -432,6 +569,14 @@ int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_al
   if (!res->eigval || !res->resid || !res->sing || !res->coef || !res->alb || !res->iters || !res->status)
     return fail(ctx, DGDFT_INVALID_ARG, "result arrays must be non-null (eigvec may be null)");
   const bool host = (prm->flags & DGDFT_HOST_BUFFERS) != 0;
+  if (prm->solver != DGDFT_CHEFSI && prm->solver != DGDFT_LOBPCG)
+    return fail(ctx, DGDFT_INVALID_ARG, "unknown solver");
+  if (prm->solver == DGDFT_LOBPCG) {
+    if (prm->precision != DGDFT_FP64) return fail(ctx, DGDFT_UNSUPPORTED, "LOBPCG runs in DGDFT_FP64");
+    for (int k = 0; k < P.M; k++)
+      if (P.desc[k].n_blk != P.desc[0].n_blk || P.desc[k].n_blk > 32)
+        return fail(ctx, DGDFT_UNSUPPORTED, "LOBPCG needs the same block size <= 32 in every element");
+  }
   const int degree = prm->cheb_degree;
   const int lsteps = prm->lanczos_steps > 0 ? prm->lanczos_steps : 10;
   if ((r = upload_plan(ctx, P, st))) return r;
@@ -506,6 +651,12 @@ int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_al
     }
     launch_final_resid(b, c.resid2, P.L, c.resid, st);
     X64 = s64.B[0];
+  } else if (prm->solver == DGDFT_LOBPCG) {
+    const int u64[4] = {0, 2, 4, 6};
+    if ((r = get_stage<double>(ctx, P, s64, 8, u64))) return r;
+    launch_random_init<double>(ball, s64.B[0], P.d_off[OFF_X], prm->seed, st);
+    if (x0) launch_convert<double, double>(ball, x0, P.d_off[OFF_E], s64.B[0], P.d_off[OFF_X], NV_EIG, st);
+    if ((r = lobpcg_stage(ctx, P, c, prm, s64.B[0], st, res->history, &X64))) return r;
   } else {
     const int u64[4] = {0, 2, 4, 6};
     if ((r = get_stage<double>(ctx, P, s64, 8, u64))) return r;

@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) k_zline(HxArgs a, cplx<T>* __restrict__ S
     if (kk < n) {
       const int m = kk <= n / 2 ? kk : kk - n;
       const double g = twopi * m / (n * d.h[ax]);
-      if (mode == MULT_KINETIC) v = T(0.5 * g * g * invN);
+      if (mode == MULT_KINETIC || mode == MULT_TETER) v = T(0.5 * g * g * invN);
       else if (mode == MULT_DX + ax) v = (n % 2 == 0 && kk == n / 2) ? T(0) : T(g * invN);
     }
     tab[i] = v;
@@ -179,6 +179,12 @@ __global__ void __launch_bounds__(256) k_zline(HxArgs a, cplx<T>* __restrict__ S
     cplx<T> s = buf[i];
     if (mode == MULT_KINETIC) {
       s = cscale(s, tab[kx] + tab[kMaxLine + ky] + tab[2 * kMaxLine + kz]);
+    } else if (mode == MULT_TETER) {
+      // Teter, Payne, Allan (1989): K(x) = (27 + 18x + 12x^2 + 8x^3) / (... + 16x^4), x = (|G|^2/2) / E_v
+      const double e = a.mref[(long long)k * a.mref_ld + v];
+      const double x = double(tab[kx] + tab[kMaxLine + ky] + tab[2 * kMaxLine + kz]) * double(d.N) / fmax(e, 1e-300);
+      const double num = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
+      s = cscale(s, T(num / (num + 16.0 * x * x * x * x) * invN));
     } else if (mode == MULT_SCALE) {
       s = cscale(s, sc);
     } else {

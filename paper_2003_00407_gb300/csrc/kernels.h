@@ -17,7 +17,9 @@ constexpr int kFusedAtomLimit = 96;
 extern long long g_launches;
 inline void count_launch() { __atomic_add_fetch(&g_launches, 1, __ATOMIC_RELAXED); }
 
-enum MultMode { MULT_KINETIC = 0, MULT_SCALE = 1, MULT_DX = 2, MULT_DY = 3, MULT_DZ = 4 };
+// spectral multipliers of the multi-pass transforms: kinetic 1/2|G|^2, plain 1/N, d/dx, d/dy, d/dz, and the
+// Teter preconditioner K(1/2|G|^2 / E_v) with E_v = HxArgs::mref[k * mref_ld + v]
+enum MultMode { MULT_KINETIC = 0, MULT_SCALE = 1, MULT_DX = 2, MULT_DY = 3, MULT_DZ = 4, MULT_TETER = 5 };
 enum OutMode { OUT_APPLY = 0, OUT_CHEB = 1, OUT_RAW = 2 };
 enum NvecMode { NV_BLK = 0, NV_EIG = 1, NV_ALB = 2, NV_ONE = 3 };
 
@@ -34,6 +36,8 @@ struct HxArgs {
   double r_cut;
   const FusedAtomRec* fatoms;  // atom records of the fused kernel
   ProjList plist;              // their compact projector-point lists
+  const double* mref;          // MULT_TETER: per (element, vector) reference kinetic energy
+  int mref_ld;
 };
 
 struct ShapeGroup {
@@ -149,6 +153,17 @@ extern thread_local int g_max_points, g_max_nblk, g_max_nalb;
 void launch_lanczos_bound(const BatchArgs& b, const double* alphas, const double* betas, int steps,
                           const double* fnorm2, double* bounds, double* lanczos_min, cudaStream_t st);
 void launch_first_a0(const BatchArgs& b, const double* lanczos_min, double* bounds, cudaStream_t st);
+
+// ---- LOBPCG local solver (k_lobpcg.cu) ----
+void launch_lobpcg_resid(const BatchArgs& b, const double* X, const double* HX, const long long* xo,
+                         const double* theta, int ld, double* W, double* resid2, cudaStream_t st);
+void launch_vec_dots(const BatchArgs& b, const double* X, const double* Y, const long long* xo, int ld, double* out,
+                     cudaStream_t st);
+void launch_scale_rows(const BatchArgs& b, double* X, double* Y, const long long* xo, const double* nrm2, int ld,
+                       cudaStream_t st);
+void launch_lobpcg_update(const BatchArgs& b, const long long* xo, const double* C, int ld, int nb, const double* X,
+                          const double* W, const double* P, const double* HX, const double* HW, const double* HP,
+                          double* Xn, double* Pn, double* HXn, double* HPn, cudaStream_t st);
 
 // ---- DG assembly (k_dg.cu) ----
 void launch_proj_overlap(const BatchArgs& b, const AtomBox* boxes, const double* dtab, const double* A,

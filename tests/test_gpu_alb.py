@@ -82,3 +82,32 @@ def test_warm_start_from_converged_vectors(ctx, precision):
     assert ic.min() >= 3
     assert iw.max() <= (1 if precision == 0 else 3), iw
     _check(w, warm, refs, range(w.problem.n_elem))
+
+
+@pytest.mark.parametrize("case", ["cube", "slab"])
+def test_lobpcg_solver_matches_the_oracle(ctx, case):
+    """The second local solver (Alg. LOBPCG with the Teter preconditioner, FP64) on the same H x kernels:
+    eigenvalues within 1e-6 Ha and ALB subspaces within 1e-5 of the oracle's dense eigensolve, residuals at
+    tol; and the same eigenvalues as the CheFSI route."""
+    from paper_2003_00407_gb300 import api, _abi
+    if case == "cube":
+        w = make_config(1)
+    else:
+        w = make_slab(3, 2, (8, 6, 12), (16, 12, 12), 0.45, 10, 6, 5, r_cut=2.6, width=0.7, proj_width=0.7)
+    p, q = w.problem, w.params
+    refs = {k: driver.solve_element(p, q, k, dense_route=True) for k in range(p.n_elem)}
+    res = api.alb_generate(ctx, p, q, precision=_abi.FP64, tol=1e-9, max_iter=400, solver=_abi.LOBPCG)
+    che = api.alb_generate(ctx, p, q, precision=_abi.FP64, cheb_degree=12, tol=1e-9, max_iter=400)
+    print("LOBPCG iterations", res.iters.cpu().numpy(), "CheFSI passes", che.iters.cpu().numpy())
+    _check(w, res, refs, range(p.n_elem))
+    n_eig = int(q.n_eig[0])
+    assert np.abs(res.eigval.cpu().numpy()[:, :n_eig] - che.eigval.cpu().numpy()[:, :n_eig]).max() <= 1e-8
+    assert res.resid.cpu().numpy()[:, :n_eig].max() <= 1e-9
+
+
+def test_lobpcg_rejects_mixed_precision_and_large_blocks(ctx):
+    from paper_2003_00407_gb300 import api, _abi
+    w = make_config(1)
+    with pytest.raises(api.DgdftError) as e:
+        api.alb_generate(ctx, w.problem, w.params, precision=_abi.MIXED, solver=_abi.LOBPCG)
+    assert "UNSUPPORTED" in str(e.value)
