@@ -313,10 +313,16 @@ int chefsi_stage(dgdft_ctx* ctx, Plan& P, const Common& c, Stage<T>& s, const dg
   launch_update_convergence(b, c.resid2, P.L, c.resid, c.theta, c.bounds, prm->tol, tol_mixed, mixed ? 1 : 0,
                             c.prevres, c.stall, c.flags, c.active, c.iters, st);
   launch_first_a0(b, c.lmin, c.bounds, st);
+  // filter degree per pass (a reading of the paper's fixed m): the requested degree on the first pass (a
+  // random block has no converged Ritz vectors to keep), then at most what the precision carries over the
+  // block's spectrum: growth cosh(m acosh|x(a0)|) <= 1e10 in FP32, 1e15 in FP64
+  const double range_log = sizeof(T) == 4 ? 23.72 : 35.23;
+  launch_pass_degree(b, c.bounds, degree, 1e300, c.active + 1, st);
   // the start Rayleigh-Ritz is not a filter pass
   for (int it = 0; it <= prm->max_iter; it++) {
     CUDA_OK(cudaMemcpyAsync(ctx->h_active, c.active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_OK(cudaStreamSynchronize(st));
+    const int deg = std::max(2, std::min(degree, ctx->h_active[1]));
     if (history) {
       double mx;
       std::memcpy(&mx, ctx->h_active + 2, sizeof(double));
@@ -332,13 +338,13 @@ int chefsi_stage(dgdft_ctx* ctx, Plan& P, const Common& c, Stage<T>& s, const dg
       CUDA_OK(cudaMemcpy(c.hitcap, hc.data(), P.M * sizeof(int), cudaMemcpyHostToDevice));
       break;
     }
-    launch_cheb_coeffs(b, c.bounds, c.cheb, degree, st);
-    launch_cheb_first<T>(b, s.B[0], s.HY, s.B[1], P.d_off[OFF_X], c.cheb, 3 * degree, st);
+    launch_cheb_coeffs(b, c.bounds, c.cheb, deg, st);
+    launch_cheb_first<T>(b, s.B[0], s.HY, s.B[1], P.d_off[OFF_X], c.cheb, 3 * deg, st);
     T* prev = s.B[0];
     T* cur = s.B[1];
     T* spare = s.B[2];
-    for (int step = 1; step < degree; step++) {
-      hx<T>(P, c, c.flags, OFF_X, NV_BLK, cur, spare, prev, s.S, c.cheb + 3 * step, 3 * degree, OUT_CHEB, st);
+    for (int step = 1; step < deg; step++) {
+      hx<T>(P, c, c.flags, OFF_X, NV_BLK, cur, spare, prev, s.S, c.cheb + 3 * step, 3 * deg, OUT_CHEB, st);
       T* t = prev;
       prev = cur;
       cur = spare;
@@ -349,6 +355,7 @@ int chefsi_stage(dgdft_ctx* ctx, Plan& P, const Common& c, Stage<T>& s, const dg
     cudaMemsetAsync(c.active, 0, 4 * sizeof(int), st);
     launch_update_convergence(b, c.resid2, P.L, c.resid, c.theta, c.bounds, prm->tol, tol_mixed, mixed ? 1 : 0,
                               c.prevres, c.stall, c.flags, c.active, c.iters, st);
+    launch_pass_degree(b, c.bounds, degree, range_log, c.active + 1, st);
   }
   CUDA_OK(cudaGetLastError());
   return DGDFT_OK;

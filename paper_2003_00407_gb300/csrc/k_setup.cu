@@ -230,6 +230,35 @@ __global__ void k_update_convergence(BatchArgs b, const double* resid2, int ldr,
   if (done) atomicAnd(&flags[k], ~EF_ACTIVE);
   else atomicAdd(active_count, 1);
 }
+// Filter degree of the next pass: the largest m <= max_degree for which the scaled Chebyshev polynomial's
+// growth over the block's spectrum, |T_m(x(a0))| = cosh(m acosh|x(a0)|), stays within range_log
+// (= acosh of the largest growth the precision carries), minimised over the active elements; one CTA.
+__global__ void k_pass_degree(BatchArgs b, const double* bounds, int max_degree, double range_log, int* out) {
+  __shared__ int red[256];
+  int m = max_degree;
+  for (int k = threadIdx.x; k < b.M; k += blockDim.x) {
+    if (b.flags && !(b.flags[k] & EF_ACTIVE)) continue;
+    const double a0 = bounds[3 * k], bl = bounds[3 * k + 1], bu = bounds[3 * k + 2];
+    const double e = 0.5 * (bu - bl), c = 0.5 * (bu + bl);
+    const double x = e > 0.0 ? fabs((a0 - c) / e) : 1.0;
+    if (x > 1.0) {
+      const double mk = floor(range_log / acosh(x));
+      if (mk < double(m)) m = int(fmax(mk, 8.0));
+    }
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = min(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = min(red[0], max_degree);
+}
+void launch_pass_degree(const BatchArgs& b, const double* bounds, int max_degree, double range_log, int* out,
+                        cudaStream_t st) {
+  count_launch(); k_pass_degree<<<1, 256, 0, st>>>(b, bounds, max_degree, range_log, out);
+}
+
 void launch_update_convergence(const BatchArgs& b, const double* resid2, int ldr, double* resid, const double* theta,
                                double* bounds, double tol, double tol_mixed, int mixed, double* prev_res, int* stall,
                                int* flags, int* active_count, int* iters, cudaStream_t st) {

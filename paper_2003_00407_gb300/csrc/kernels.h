@@ -130,6 +130,8 @@ void launch_setup_v(const BatchArgs& b, const AtomBox* boxes, const double* dtab
 void launch_restrict(const BatchArgs& b, const double* X, const long long* xo, double* XE, const long long* eo,
                      int nvec_mode, cudaStream_t st);
 void launch_alb_sign(const BatchArgs& b, double* A, const long long* ao, double* C, int ldc, cudaStream_t st);
+void launch_pass_degree(const BatchArgs& b, const double* bounds, int max_degree, double range_log, int* out,
+                        cudaStream_t st);
 void launch_update_convergence(const BatchArgs& b, const double* resid2, int ldr, double* resid, const double* theta,
                                double* bounds, double tol, double tol_mixed, int mixed, double* prev_res,
                                int* stall, int* flags, int* active_count, int* iters, cudaStream_t st);

@@ -9,7 +9,7 @@ assembled into the dense N_b x N_b matrix (N_b = 64 x 32 = 2048, Eq. DGEigenvalu
   off-diagonal blocks (basis-invariant: an orthogonal change of ALB basis inside an element leaves them
   unchanged);
 * the largest asymmetry |H - H^T| of the assembled matrix;
-* the DG solution of the lowest 64 states with 32 electrons at kT = 0.01 Ha (Eq. density with the diagonal
+* the DG solution of the lowest 64 states with 32 electrons at kT = 0.005 Ha (Eq. density with the diagonal
   density-matrix blocks, the band energy of Eq. DGvar, the Hellmann-Feynman gradient of Eq. hfforce at
   fixed ALBs): band energy, mu, the integral of the density, its values at 64 seeded grid points, and the
   atom gradient.
@@ -34,7 +34,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 DEGREE, TOL, MAX_ITER = 30, 1e-10, 150
 N_LOW = 64
-DG_NEL, DG_KT = 32.0, 0.01
+DG_NEL, DG_KT = 32.0, 0.005
 PROBE_SEED = 5151
 
 
