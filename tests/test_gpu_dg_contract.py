@@ -215,7 +215,7 @@ def test_whole_box_dg_eigensolve_matches_the_oracle_solver(ctx):
 
 
 def test_c2_dg_density_energy_and_forces(ctx):
-    """The DG solution of the c2 slab on the GPU (64 states, 32 electrons, kT 0.01 Ha) from FP64 ALBs:
+    """The DG solution of the c2 slab on the GPU (64 states, 32 electrons, kT 0.005 Ha) from FP64 ALBs:
     band energy and mu within 1e-6 Ha of the oracle golden, the density at 64 grid points within 1e-6 of
     its maximum, the charge within 1e-9, the Hellmann-Feynman gradient within 1e-5 of its largest entry."""
     from paper_2003_00407_gb300 import api
