@@ -9,7 +9,8 @@ generation for every element followed by the interior-penalty DG assembly
 
 The JSON line also carries: the roofline of the Chebyshev filter step (timed
 live with CUDA events on its stream), the end-to-end number through the C-ABI
-with host buffers, the FP64 GPU path on a sample of elements, the oracle timed
+with host buffers, the FP64 GPU path on a sample of elements, the uneven
+256-element batch (15 Q shapes) in elements/s, the oracle timed
 on the host cores (a baseline, not the target), SM clocks sampled during the
 timed region and the number of kernel launches.
 
@@ -49,6 +50,7 @@ def parse():
     ap.add_argument("--fp64-elements", type=int, default=128, help="elements in the FP64 GPU sample (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true", help="skip the 256-element uneven-batch measurement")
     ap.add_argument("--cpu-elements", type=int, default=0,
                     help="elements the oracle baseline solves (0 = two per host process)")
     ap.add_argument("--elements", type=int, default=0, help="use only the first n elements (smoke runs)")
@@ -336,6 +338,31 @@ def run_native(args, wl, rank, world, local_rank):
         # per filter pass and element: separates per-iteration speed from convergence
         fp64["ms_per_pass_per_element"] = 1000 * t64 / max(fp64["iterations_mean"], 1e-9) / ns
 
+    # ---- the uneven batch: 256 independent elements of 15 Q shapes (one untimed pass first) ----
+    uneven = None
+    if not args.no_uneven:
+        from workloads import make_config
+        wu = make_config(3)
+        pu, qu = wu.problem, wu.params
+        for rep in range(2):
+            barrier()
+            u0, u1, u2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            u0.record(stream)
+            ru = api.alb_generate(ctx, pu, qu, precision=_abi.MIXED, cheb_degree=args.degree, tol=args.tol,
+                                  max_iter=args.max_iter, keep_eigvec=False)
+            u1.record(stream)
+            api.dg_assemble(ctx, pu, qu, ru, wu.alpha)
+            u2.record(stream)
+            torch.cuda.synchronize()
+        shapes = {tuple(int(v) for v in qn) for qn in pu.elem_Qn}
+        tu = u0.elapsed_time(u2) / 1000.0
+        uneven = {"value": pu.n_elem / tu, "unit": UNIT,
+                  "workload": f"{pu.n_elem} independent elements of {len(shapes)} Q shapes "
+                              "({24,32,40}^2 x {32,48}), 20-60 ALBs, mixed precision (second of two passes)",
+                  "alb_ms": u0.elapsed_time(u1), "dg_ms": u1.elapsed_time(u2),
+                  "iterations_mean": float(np.mean(ru.iters.cpu().numpy())),
+                  "status_nonzero": int(np.count_nonzero(ru.status.cpu().numpy()))}
+
     out = None
     if rank == 0:
         if cpu is not None:
@@ -344,7 +371,7 @@ def run_native(args, wl, rank, world, local_rank):
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config_dict(args, wl),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-               "clocks": clk.summary(), "fp64_gpu": fp64,
+               "clocks": clk.summary(), "fp64_gpu": fp64, "uneven_batch": uneven,
                "phase_ms": {"alb_generate": t_alb, "dg_assemble": t_dg},
                "iterations": {"mean": float(iters.mean()), "max": int(iters.max()),
                               "ms_per_pass_per_element": t_alb / max(float(iters.mean()), 1e-9) / M},

@@ -182,6 +182,45 @@ int64_t dgdft_kernel_launches(void);
 int dgdft_stage_converged(double max_resid, double tol, double tol_mixed, int mixed, double b_up, double* prev_resid,
                           int* stall);
 
+/* Gram matrices of FP32 vector blocks on the tensor cores: for every block k,
+ *   G_k[i][j] = dV_k sum_p X_k[i][p] Y_k[j][p]      (i < nx[k], j < ny[k], p < np[k])
+ * the overlap X^T X of the Cholesky-QR step and the projection X^T (H X) of the Rayleigh-Ritz step of
+ * Alg. CheFSI, as the FP32 stage of dgdft_alb_generate forms them (the same kernel).  Each input is split
+ * into two TF32 parts (x = x_hi + x_lo); the products x_hi y_hi + x_hi y_lo + x_lo y_hi run on
+ * tcgen05 tensor cores with FP32 accumulation over 512 points, the partial sums are added exactly
+ * (two-sum) over 4096 points and in FP64 beyond.  Error: a few 2^-22 of dV_k sum_p |X_k[i][p]| |Y_k[j][p]|.
+ *   n_blocks             number of blocks (0: nothing to do)
+ *   nx, ny, np, dV       host arrays [n_blocks]: rows of X_k (0..96), rows of Y_k (0..96), points, volume element
+ *   X, Y                 device FP32: X_k row-major [nx[k]][np[k]] starting at X + x_off[k] (Y likewise; Y may be X)
+ *   x_off, y_off         host arrays [n_blocks] of element offsets (>= 0)
+ *   G                    device FP64 [n_blocks][ldg][ldg], overwritten (entries outside the nx x ny block are 0)
+ *   ldg                  >= every nx[k] and ny[k]
+ *   stream               CUDA stream; the call returns after the work on it has completed
+ * Uses the context's grow-only workspace for the block table.  Errors: DGDFT_INVALID_ARG (null pointers,
+ * counts or offsets out of range), DGDFT_CUDA_ERROR (including a bounded tensor-core wait that ran out). */
+int dgdft_gram_fp32(dgdft_ctx* ctx, int n_blocks, const int* nx, const int* ny, const int* np, const double* dV,
+                    const float* X, const int64_t* x_off, const float* Y, const int64_t* y_off, double* G, int ldg,
+                    dgdft_stream stream);
+
+/* Subspace rotation of FP32 vector blocks on the tensor cores: for every block k,
+ *   Z_k[j][p] = sum_i W_k[i][j] X_k[i][p]          (j < nout[k], i < nin[k], p < np[k])
+ * the X <- X U^-1 step of Cholesky-QR and the X <- X C step of Rayleigh-Ritz of Alg. CheFSI, as the FP32
+ * stage of dgdft_alb_generate applies them (the same kernel).  X and W are split into two TF32 parts each
+ * (3xTF32 products on tcgen05 tensor cores, FP32 accumulation over the nin terms).  Error: a few 2^-22
+ * of sum_i |W_k[i][j]| |X_k[i][p]|.
+ *   n_blocks               number of blocks (0: nothing to do)
+ *   nin, nout, np          host arrays [n_blocks]: input vectors (0..96), output vectors (0..96), points
+ *   X                      device FP32: X_k row-major [nin[k]][np[k]] at X + x_off[k]
+ *   W                      device FP64 [n_blocks][ldw][ldw], row i of block k = input vector i
+ *   Z                      device FP32: Z_k [nout[k]][np[k]] at Z + z_off[k]; Z may be X (in place, same offsets)
+ *   x_off, z_off           host arrays [n_blocks] of element offsets (>= 0)
+ *   stream                 CUDA stream; the call returns after the work on it has completed
+ * Uses the context's grow-only workspace for the block table.  Errors: DGDFT_INVALID_ARG (null pointers,
+ * counts or offsets out of range), DGDFT_CUDA_ERROR (including a bounded tensor-core wait that ran out). */
+int dgdft_rotate_fp32(dgdft_ctx* ctx, int n_blocks, const int* nin, const int* nout, const int* np, const float* X,
+                      const int64_t* x_off, const double* W, int ldw, float* Z, const int64_t* z_off,
+                      dgdft_stream stream);
+
 /* ALB generation for all elements in one batched solve: the lowest n_eig eigenpairs of each local
  * Hamiltonian (Eq. LocalKS) by Chebyshev-filtered subspace iteration (Alg. CheFSI: Lanczos upper bound,
  * scaled Chebyshev filter, Cholesky-QR, Rayleigh-Ritz; in DGDFT_MIXED an FP32 stage, then one FP64

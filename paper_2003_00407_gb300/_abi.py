@@ -73,6 +73,10 @@ FUNCTIONS = {
                                    C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p]),
     "dgdft_stage_converged": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, PD, PI]),
+    "dgdft_gram_fp32": (C.c_int, [C.c_void_p, C.c_int, PI, PI, PI, PD, C.c_void_p, PL, C.c_void_p, PL, C.c_void_p,
+                                  C.c_int, C.c_void_p]),
+    "dgdft_rotate_fp32": (C.c_int, [C.c_void_p, C.c_int, PI, PI, PI, C.c_void_p, PL, C.c_void_p, C.c_int, C.c_void_p,
+                                    PL, C.c_void_p]),
     "dgdft_apply_hamiltonian_noalloc": (C.c_int, [C.POINTER(Problem), C.POINTER(AlbParams), C.c_void_p, C.c_void_p,
                                                   C.c_void_p]),
 }

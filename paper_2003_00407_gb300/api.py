@@ -211,6 +211,43 @@ def apply_hamiltonian(ctx: Context, prob, params, X: torch.Tensor, precision=_ab
     return Y
 
 
+def gram_fp32(ctx: Context, X: torch.Tensor, x_off, nx, np_, dV, Y: torch.Tensor = None, y_off=None, ny=None,
+              ldg=None):
+    """G_k = dV_k X_k Y_k^T for packed FP32 blocks on the tensor cores (3xTF32); returns [n][ldg][ldg] FP64."""
+    n = len(nx)
+    if Y is None:
+        Y, y_off, ny = X, x_off, nx
+    nx_, ny_, npp = _i32(nx), _i32(ny), _i32(np_)
+    dv = _f64(dV)
+    xo = np.ascontiguousarray(x_off, dtype=np.int64)
+    yo = np.ascontiguousarray(y_off, dtype=np.int64)
+    ldg = int(ldg or max(1, int(max(nx_.max(initial=0), ny_.max(initial=0)))))
+    G = torch.empty((n, ldg, ldg), dtype=torch.float64, device=X.device)
+    ctx.check(ctx.lib.dgdft_gram_fp32(ctx.h, n, _ptr(nx_, C.c_int), _ptr(ny_, C.c_int), _ptr(npp, C.c_int),
+                                      _ptr(dv, C.c_double), C.c_void_p(X.data_ptr()), _ptr(xo, C.c_int64),
+                                      C.c_void_p(Y.data_ptr()), _ptr(yo, C.c_int64), C.c_void_p(G.data_ptr()), ldg,
+                                      _stream()))
+    return G
+
+
+def rotate_fp32(ctx: Context, X: torch.Tensor, x_off, nin, np_, W: torch.Tensor, nout, Z: torch.Tensor = None,
+                z_off=None):
+    """Z_k = W_k^T X_k for packed FP32 blocks on the tensor cores (3xTF32); W [n][ldw][ldw] FP64 on the device.
+    Z defaults to a new packed tensor with the output blocks back to back."""
+    n = len(nin)
+    ni, no, npp = _i32(nin), _i32(nout), _i32(np_)
+    xo = np.ascontiguousarray(x_off, dtype=np.int64)
+    if Z is None:
+        sizes = no.astype(np.int64) * npp
+        z_off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+        Z = torch.empty(int(sizes.sum()), dtype=torch.float32, device=X.device)
+    zo = np.ascontiguousarray(z_off, dtype=np.int64)
+    ctx.check(ctx.lib.dgdft_rotate_fp32(ctx.h, n, _ptr(ni, C.c_int), _ptr(no, C.c_int), _ptr(npp, C.c_int),
+                                        C.c_void_p(X.data_ptr()), _ptr(xo, C.c_int64), C.c_void_p(W.data_ptr()),
+                                        int(W.shape[-1]), C.c_void_p(Z.data_ptr()), _ptr(zo, C.c_int64), _stream()))
+    return Z, zo
+
+
 def chebyshev_filter(ctx: Context, prob, params, X: torch.Tensor, bounds: np.ndarray, degree: int,
                      precision=_abi.FP64):
     """Y = p_m(H) X with per-element bounds (a0, b_low, b_up)."""

@@ -97,10 +97,9 @@ int upload_plan(dgdft_ctx* ctx, Plan& P, cudaStream_t st) {
   {
     // compact projector-point lists of the Q boxes (read by the fused kernel)
     const size_t nq = size_t(std::max(1, P.n_qboxes));
-    P.plist.g = (float*)ws(ctx, "p_plist_g", nq * kProjCap * sizeof(float));
-    P.plist.w = (unsigned*)ws(ctx, "p_plist_w", nq * kProjCap * sizeof(unsigned));
-    P.plist.n = (int*)ws(ctx, "p_plist_n", nq * sizeof(int));
-    if (!P.plist.g || !P.plist.w || !P.plist.n) return fail(ctx, DGDFT_OUT_OF_MEMORY, "workspace allocation failed: p_plist");
+    P.plist.gw = (uint2*)ws(ctx, "p_plist_gw", nq * kProjCap * sizeof(uint2));
+    P.plist.n = (int*)ws(ctx, "p_plist_n", 2 * nq * sizeof(int));
+    if (!P.plist.gw || !P.plist.n) return fail(ctx, DGDFT_OUT_OF_MEMORY, "workspace allocation failed: p_plist");
     if (P.n_qboxes > 0) launch_build_proj_lists(P.d_fatoms, P.d_dtab, P.n_qboxes, P.r_cut, P.plist, st);
   }
   const char* names[kOffKinds] = {"p_ox", "p_oe", "p_oa", "p_ov", "p_os", "p_ofe", "p_ove"};
@@ -149,7 +148,7 @@ template <typename T> struct Stage {
 struct Common {
   double *V64, *bounds, *cheb, *G1, *G2, *W, *theta, *resid2, *resid, *P, *prevres, *alphas, *betas, *ldot, *lmin;
   float* V32;
-  int *flags, *iters, *stall, *active, *hitcap;
+  int *flags, *iters, *stall, *active, *hitcap, *pdeg;
 };
 
 #define WS(ptr, name, bytes)                                                             \
@@ -214,6 +213,7 @@ int get_common(dgdft_ctx* ctx, const Plan& P, int degree, int lsteps, Common& c)
   WS(c.stall, "stall", M * sizeof(int));
   WS(c.active, "active", 4 * sizeof(int));   // [0] active count, [2..3] max residual (double bits)
   WS(c.hitcap, "hitcap", M * sizeof(int));
+  WS(c.pdeg, "pdeg", M * sizeof(int));
   return DGDFT_OK;
 }
 
@@ -313,11 +313,12 @@ int chefsi_stage(dgdft_ctx* ctx, Plan& P, const Common& c, Stage<T>& s, const dg
   launch_update_convergence(b, c.resid2, P.L, c.resid, c.theta, c.bounds, prm->tol, tol_mixed, mixed ? 1 : 0,
                             c.prevres, c.stall, c.flags, c.active, c.iters, st);
   launch_first_a0(b, c.lmin, c.bounds, st);
-  // filter degree per pass (a reading of the paper's fixed m): the requested degree on the first pass (a
-  // random block has no converged Ritz vectors to keep), then at most what the precision carries over the
-  // block's spectrum: growth cosh(m acosh|x(a0)|) <= 1e10 in FP32, 1e15 in FP64
+  // filter degree per pass and element (a reading of the paper's fixed m): the requested degree on the first
+  // pass (a random block has no converged Ritz vectors to keep), then at most what the precision carries
+  // over the element's spectrum: growth cosh(m acosh|x(a0)|) <= 1e10 in FP32, 1e15 in FP64; the pass runs
+  // the largest of these and elements with a smaller one stop early
   const double range_log = sizeof(T) == 4 ? 23.72 : 35.23;
-  launch_pass_degree(b, c.bounds, degree, 1e300, c.active + 1, st);
+  launch_pass_degree(b, c.bounds, degree, 1e300, c.pdeg, c.active + 1, st);
   // the start Rayleigh-Ritz is not a filter pass
   for (int it = 0; it <= prm->max_iter; it++) {
     CUDA_OK(cudaMemcpyAsync(ctx->h_active, c.active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -338,7 +339,7 @@ int chefsi_stage(dgdft_ctx* ctx, Plan& P, const Common& c, Stage<T>& s, const dg
       CUDA_OK(cudaMemcpy(c.hitcap, hc.data(), P.M * sizeof(int), cudaMemcpyHostToDevice));
       break;
     }
-    launch_cheb_coeffs(b, c.bounds, c.cheb, deg, st);
+    launch_cheb_coeffs(b, c.bounds, c.cheb, deg, st, c.pdeg);
     launch_cheb_first<T>(b, s.B[0], s.HY, s.B[1], P.d_off[OFF_X], c.cheb, 3 * deg, st);
     T* prev = s.B[0];
     T* cur = s.B[1];
@@ -355,7 +356,7 @@ int chefsi_stage(dgdft_ctx* ctx, Plan& P, const Common& c, Stage<T>& s, const dg
     cudaMemsetAsync(c.active, 0, 4 * sizeof(int), st);
     launch_update_convergence(b, c.resid2, P.L, c.resid, c.theta, c.bounds, prm->tol, tol_mixed, mixed ? 1 : 0,
                               c.prevres, c.stall, c.flags, c.active, c.iters, st);
-    launch_pass_degree(b, c.bounds, degree, range_log, c.active + 1, st);
+    launch_pass_degree(b, c.bounds, degree, range_log, c.pdeg, c.active + 1, st);
   }
   CUDA_OK(cudaGetLastError());
   return DGDFT_OK;
@@ -564,6 +565,100 @@ int dgdft_stage_converged(double max_resid, double tol, double tol_mixed, int mi
   return stage_converged(max_resid, tol, tol_mixed, mixed, b_up, prev_resid, stall);
 }
 
+int dgdft_gram_fp32(dgdft_ctx* ctx, int n_blocks, const int* nx, const int* ny, const int* np, const double* dV,
+                    const float* X, const int64_t* x_off, const float* Y, const int64_t* y_off, double* G, int ldg,
+                    dgdft_stream stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!ctx || n_blocks < 0 || (n_blocks > 0 && (!nx || !ny || !np || !dV || !X || !x_off || !Y || !y_off || !G)))
+    return fail(ctx, DGDFT_INVALID_ARG, "dgdft_gram_fp32: null argument or negative block count");
+  if (n_blocks == 0) return DGDFT_OK;
+  int max_rows = 0, max_np = 0;
+  for (int k = 0; k < n_blocks; k++) {
+    if (nx[k] < 0 || ny[k] < 0 || np[k] < 0 || nx[k] > 96 || ny[k] > 96 || nx[k] > ldg || ny[k] > ldg ||
+        x_off[k] < 0 || y_off[k] < 0)
+      return fail(ctx, DGDFT_INVALID_ARG, "dgdft_gram_fp32: block " + std::to_string(k) +
+                                              ": rows outside 0..min(96, ldg) or a negative count or offset");
+    max_rows = std::max(max_rows, std::max(nx[k], ny[k]));
+    max_np = std::max(max_np, np[k]);
+  }
+  CUDA_OK(cudaSetDevice(ctx->device));
+  // block k as an element descriptor: rows of X in n_blk, rows of Y in n_eig, points in N
+  std::vector<ElemDesc> hd(n_blocks);
+  std::vector<long long> ho(2 * n_blocks);
+  for (int k = 0; k < n_blocks; k++) {
+    hd[k] = ElemDesc{};
+    hd[k].n_blk = nx[k];
+    hd[k].n_eig = ny[k];
+    hd[k].N = np[k];
+    hd[k].dV = dV[k];
+    ho[k] = x_off[k];
+    ho[n_blocks + k] = y_off[k];
+  }
+  ElemDesc* dd = (ElemDesc*)ws(ctx, "gram_desc", n_blocks * sizeof(ElemDesc));
+  long long* doff = (long long*)ws(ctx, "gram_off", 2 * n_blocks * sizeof(long long));
+  if (!dd || !doff) return fail(ctx, DGDFT_OUT_OF_MEMORY, "dgdft_gram_fp32: workspace allocation failed");
+  CUDA_OK(cudaMemcpyAsync(dd, hd.data(), n_blocks * sizeof(ElemDesc), cudaMemcpyHostToDevice, st));
+  CUDA_OK(cudaMemcpyAsync(doff, ho.data(), 2 * n_blocks * sizeof(long long), cudaMemcpyHostToDevice, st));
+  CUDA_OK(cudaMemsetAsync(G, 0, (size_t)n_blocks * ldg * ldg * sizeof(double), st));
+  g_max_points = max_np;
+  g_max_nblk = max_rows;
+  g_max_nalb = 0;
+  BatchArgs b{dd, nullptr, n_blocks};
+  if (max_rows > 0 && max_np > 0 &&
+      !launch_gram_tc(b, X, doff, NV_BLK, Y, doff + n_blocks, NV_EIG, 4, G, ldg, st, 1.0, max_rows))
+    return fail(ctx, DGDFT_UNSUPPORTED, "dgdft_gram_fp32: block shape not handled");
+  CUDA_OK(cudaGetLastError());
+  CUDA_OK(cudaStreamSynchronize(st));
+  if (take_tc_error()) return fail(ctx, DGDFT_CUDA_ERROR, "dgdft_gram_fp32: a tensor-core wait ran out");
+  return DGDFT_OK;
+}
+
+int dgdft_rotate_fp32(dgdft_ctx* ctx, int n_blocks, const int* nin, const int* nout, const int* np, const float* X,
+                      const int64_t* x_off, const double* W, int ldw, float* Z, const int64_t* z_off,
+                      dgdft_stream stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!ctx || n_blocks < 0 || (n_blocks > 0 && (!nin || !nout || !np || !X || !x_off || !W || !Z || !z_off)))
+    return fail(ctx, DGDFT_INVALID_ARG, "dgdft_rotate_fp32: null argument or negative block count");
+  if (n_blocks == 0) return DGDFT_OK;
+  int max_rows = 0, max_np = 0;
+  for (int k = 0; k < n_blocks; k++) {
+    if (nin[k] < 0 || nout[k] < 0 || np[k] < 0 || nin[k] > 96 || nout[k] > 96 || nin[k] > ldw || nout[k] > ldw ||
+        x_off[k] < 0 || z_off[k] < 0)
+      return fail(ctx, DGDFT_INVALID_ARG, "dgdft_rotate_fp32: block " + std::to_string(k) +
+                                              ": vectors outside 0..min(96, ldw) or a negative count or offset");
+    max_rows = std::max(max_rows, std::max(nin[k], nout[k]));
+    max_np = std::max(max_np, np[k]);
+  }
+  CUDA_OK(cudaSetDevice(ctx->device));
+  std::vector<ElemDesc> hd(n_blocks);
+  std::vector<long long> ho(2 * n_blocks);
+  for (int k = 0; k < n_blocks; k++) {
+    hd[k] = ElemDesc{};
+    hd[k].n_blk = nin[k];
+    hd[k].n_eig = nout[k];
+    hd[k].N = np[k];
+    ho[k] = x_off[k];
+    ho[n_blocks + k] = z_off[k];
+  }
+  ElemDesc* dd = (ElemDesc*)ws(ctx, "rot_desc", n_blocks * sizeof(ElemDesc));
+  long long* doff = (long long*)ws(ctx, "rot_off", 2 * n_blocks * sizeof(long long));
+  if (!dd || !doff) return fail(ctx, DGDFT_OUT_OF_MEMORY, "dgdft_rotate_fp32: workspace allocation failed");
+  CUDA_OK(cudaMemcpyAsync(dd, hd.data(), n_blocks * sizeof(ElemDesc), cudaMemcpyHostToDevice, st));
+  CUDA_OK(cudaMemcpyAsync(doff, ho.data(), 2 * n_blocks * sizeof(long long), cudaMemcpyHostToDevice, st));
+  g_max_points = max_np;
+  g_max_nblk = max_rows;
+  g_max_nalb = 0;
+  BatchArgs b{dd, nullptr, n_blocks};
+  if (max_rows > 0 && max_np > 0 &&
+      !launch_rotate_tc(b, X, doff, Z, doff + n_blocks, NV_BLK, NV_EIG, 4, W, ldw, nullptr, nullptr, nullptr, nullptr,
+                        0, st, max_rows))
+    return fail(ctx, DGDFT_UNSUPPORTED, "dgdft_rotate_fp32: block shape not handled");
+  CUDA_OK(cudaGetLastError());
+  CUDA_OK(cudaStreamSynchronize(st));
+  if (take_tc_error()) return fail(ctx, DGDFT_CUDA_ERROR, "dgdft_rotate_fp32: a tensor-core wait ran out");
+  return DGDFT_OK;
+}
+
 int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_alb_params* prm,
                        dgdft_alb_result* res, dgdft_stream stream) {
   if (!ctx || !prob || !prm || !res) return fail(ctx, DGDFT_INVALID_ARG, "null argument");
@@ -672,6 +767,10 @@ int dgdft_alb_generate(dgdft_ctx* ctx, const dgdft_problem* prob, const dgdft_al
     X64 = s64.B[0];
   }
   CUDA_OK(cudaGetLastError());
+  if (prm->precision != DGDFT_FP64) {
+    CUDA_OK(cudaStreamSynchronize(st));
+    if (take_tc_error()) return fail(ctx, DGDFT_CUDA_ERROR, "a bounded tensor-core wait of the FP32 Gram ran out");
+  }
 
   // ---- outputs ----
   double *d_eigval = res->eigval, *d_resid = res->resid, *d_sing = res->sing, *d_coef = res->coef, *d_alb = res->alb;
@@ -844,10 +943,12 @@ static int dg_ingredients_dev(dgdft_ctx* ctx, Plan& P, const Common& c, const do
   CUDA_OK(cudaMemsetAsync(KV, 0, M * L * L * sizeof(double), st));
   set_group_nvec(P, NV_ALB);
   HxArgs ha = hx_args(P, nullptr, OFF_E, NV_ALB);
+  // one forward pass along x and y for the three axes: d/dx and d/dy need no z transform (their multiplier
+  // does not depend on k_z) and are applied as the inverse pass reads the spectrum; d/dz last, in place
+  launch_forward<double>(P.hx, ha, Psi, S, st);
   for (int axis = 0; axis < 3; axis++) {
-    launch_forward<double>(P.hx, ha, Psi, S, st);
-    launch_zline<double>(P.hx, ha, S, MULT_DX + axis, st);
-    launch_inverse_raw<double>(P.hx, ha, S, D, st);
+    if (axis == 2) launch_zline<double>(P.hx, ha, S, MULT_DZ, st);
+    launch_inverse_raw<double>(P.hx, ha, S, D, st, axis < 2 ? axis : -1);
     launch_restrict(b, D, oe, PsiE, ofe, NV_ALB, st);
     launch_gram<double>(b, PsiE, ofe, NV_ALB, PsiE, ofe, NV_ALB, 5, nullptr, nullptr, KV, P.L, st, 0.5);
   }

@@ -53,13 +53,15 @@ struct FusedAtomRec {
 };
 
 // Compact projector-point lists, one slot of kProjCap entries per fused atom record: the box points of
-// Q inside the support ball, in (z, y, x) order.  g = exp(-d^2 / 2 sigma^2) (1 - d^2/r_cut^2)^3 and
-// w = (smem float index of the point in the fused kernel's row layout) | ix << 16 | iy << 20 | iz << 24;
-// n[r] = number of points of record r.
+// Q inside the support ball in (z, y, x) order, one 64-bit entry (bits of g, w) per point:
+// g = exp(-d^2 / 2 sigma^2) (1 - d^2/r_cut^2)^3 and
+// w = (float index of the point in the fused kernel's row layout) | ix << 16 | iy << 20 | iz << 24;
+// n[2r] = number of points of record r, n[2r + 1] = 0.  For Q shapes whose vectors are split over a CTA
+// pair by plane parity: the points on even z planes first, then those on odd planes, indexed in the row
+// layout of the planes of their parity (plane z at slot z / 2), n[2r] and n[2r + 1] their numbers.
 constexpr int kProjCap = 4096;
 struct ProjList {
-  float* g;
-  unsigned* w;
+  uint2* gw;
   int* n;
 };
 

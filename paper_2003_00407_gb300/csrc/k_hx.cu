@@ -205,7 +205,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_plane_inverse(HxArgs a, const cplx<T>* __restrict__ S, const T* __restrict__ X,
                                                        const T* __restrict__ V, const double* __restrict__ P,
                                                        T* __restrict__ Y, const T* __restrict__ Yprev,
-                                                       const double* __restrict__ cheb, int cheb_stride, int out_mode) {
+                                                       const double* __restrict__ cheb, int cheb_stride, int out_mode,
+                                                       int deriv = -1) {
   const int k = a.elems[blockIdx.z];
   const ElemDesc& d = a.desc[k];
   const int v = blockIdx.y, z = blockIdx.x;
@@ -224,7 +225,21 @@ __global__ void __launch_bounds__(256) k_plane_inverse(HxArgs a, const cplx<T>* 
   __shared__ int na_list;
   __shared__ T acoef[kMaxPlaneAtoms][6];  // gamma_l N_l <b_l, x> for s, px, py, pz; 1/(2 sigma^2)
   const cplx<T>* sp = S + a.so[k] + (long long)v * d.qn[2] * qy * hx + (long long)z * qy * hx;
-  for (int i = threadIdx.x; i < qy * hx; i += blockDim.x) Sp[i] = sp[i];
+  if (deriv < 0) {
+    for (int i = threadIdx.x; i < qy * hx; i += blockDim.x) Sp[i] = sp[i];
+  } else {
+    // d/dx or d/dy of a spectrum transformed along x and y only (z still real): i G_a / (qx qy) (Nyquist
+    // dropped), the same as the z-line pass with the derivative multiplier, whose z transforms cancel
+    const int n = deriv == 0 ? qx : qy;
+    const double f = 6.283185307179586476925 / (n * d.h[deriv]) / (double(qx) * double(qy));
+    for (int i = threadIdx.x; i < qy * hx; i += blockDim.x) {
+      const int kk = deriv == 0 ? i % hx : i / hx;
+      const int m = kk <= n / 2 ? kk : kk - n;
+      const T g = (n % 2 == 0 && kk == n / 2) ? T(0) : T(f * m);
+      const cplx<T> s = sp[i];
+      Sp[i] = cplx<T>{-s.im * g, s.re * g};
+    }
+  }
   if (threadIdx.x == 0) {
     // atom boxes that meet this plane (for the nonlocal term)
     int n = 0;
@@ -363,13 +378,13 @@ void launch_zline(const HxPlan& pl, const HxArgs& args, cplx<T>* S, int mult_mod
 }
 
 template <typename T>
-void launch_inverse_raw(const HxPlan& pl, const HxArgs& args, const cplx<T>* S, T* Y, cudaStream_t st) {
+void launch_inverse_raw(const HxPlan& pl, const HxArgs& args, const cplx<T>* S, T* Y, cudaStream_t st, int deriv) {
   for (const ShapeGroup& g : pl.groups) {
     HxArgs a = args;
     a.elems = g.d_elems;
     dim3 gA(g.qn[2], g.max_nvec, g.n_elems);
     count_launch(); k_plane_inverse<T><<<gA, 256, plane_smem_bytes(g.qn[0], g.qn[1], sizeof(T)), st>>>(
-        a, S, nullptr, nullptr, nullptr, Y, nullptr, nullptr, 0, OUT_RAW);
+        a, S, nullptr, nullptr, nullptr, Y, nullptr, nullptr, 0, OUT_RAW, deriv);
   }
 }
 
@@ -390,6 +405,6 @@ template void launch_hx<double>(const HxPlan&, const HxArgs&, const double*, dou
                                 cplx<double>*, double*, const double*, int, int, int, cudaStream_t);
 template void launch_forward<double>(const HxPlan&, const HxArgs&, const double*, cplx<double>*, cudaStream_t);
 template void launch_zline<double>(const HxPlan&, const HxArgs&, cplx<double>*, int, cudaStream_t);
-template void launch_inverse_raw<double>(const HxPlan&, const HxArgs&, const cplx<double>*, double*, cudaStream_t);
+template void launch_inverse_raw<double>(const HxPlan&, const HxArgs&, const cplx<double>*, double*, cudaStream_t, int);
 
 }  // namespace dgdft

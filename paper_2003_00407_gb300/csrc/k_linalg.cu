@@ -3,7 +3,9 @@
 // rotations (step 5) with fused residual norms, and the small dense solvers
 // (Cholesky + triangular inverse, symmetric eigensolver) run one CTA per
 // element in shared memory.  All small matrices are FP64.
+#include <algorithm>
 #include <cstdio>
+#include <type_traits>
 #include "kernels.h"
 
 namespace dgdft {
@@ -116,7 +118,12 @@ void launch_gram(const BatchArgs& b, const TI* A, const long long* ao, int na_mo
                  int nb_mode, int npts_mode, const double* weight, const long long* wo, double* G, int ldg,
                  cudaStream_t st, double scale) {
   // callers zero G first
-
+  if constexpr (std::is_same<TI, float>::value) {
+    // FP32 inputs: 3xTF32 on the tensor cores (k_gram_tc.cu)
+    if (weight == nullptr &&
+        launch_gram_tc(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, G, ldg, st, scale, std::max(g_max_nblk, g_max_nalb)))
+      return;
+  }
   dim3 grid((g_max_points + kGramChunk - 1) / kGramChunk, b.M);
   count_launch();
   switch (tile_r(g_max_nblk)) {
@@ -246,6 +253,12 @@ template <typename TX, typename TZ>
 void launch_rotate(const BatchArgs& b, const TX* X, const long long* xo, TZ* Z, const long long* zo, int nin_mode,
                    int nout_mode, int npts_mode, const double* W, int ldw, const TX* X2, TZ* Z2, const double* theta,
                    double* resid2, int ldr, cudaStream_t st) {
+  if constexpr (std::is_same<TX, float>::value && std::is_same<TZ, float>::value) {
+    // FP32 blocks: 3xTF32 on the tensor cores (k_gram_tc.cu)
+    if (launch_rotate_tc(b, X, xo, Z, zo, nin_mode, nout_mode, npts_mode, W, ldw, X2, Z2, theta, resid2, ldr, st,
+                         std::max(g_max_nblk, g_max_nalb)))
+      return;
+  }
   constexpr int Q = rot_q<TX>();
   const int pts = kRotTiles * 16 * Q;
   dim3 grid((g_max_points + pts - 1) / pts, b.M);

@@ -82,7 +82,9 @@ thread_local int g_max_nblk = 0;
 // ---- Chebyshev filter coefficients (scaled three-term recurrence) ----
 // bounds[k] = {a0, b_low, b_up}; step 1: Y = (s1/e)(H - c)X;
 // step i>1: s' = 1/(2/s1 - s), Y' = (2 s'/e)(H - c)Y - s s' Y_prev.
-__global__ void k_cheb_coeffs(BatchArgs b, const double* bounds, double* cheb, int degree) {
+// Steps i >= pdeg[k] (when given) get alpha = 0, beta = 1: y_{i+1} = y_{i-1}, so that the element's block
+// stays at y_{pdeg[k]} after the pass (D - pdeg[k] even) while the others run on.
+__global__ void k_cheb_coeffs(BatchArgs b, const double* bounds, double* cheb, int degree, const int* pdeg) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.M) return;
   const double a0 = bounds[3 * k], bl = bounds[3 * k + 1], bu = bounds[3 * k + 2];
@@ -98,9 +100,16 @@ __global__ void k_cheb_coeffs(BatchArgs b, const double* bounds, double* cheb, i
     ck[3 * i + 2] = -sigma * sn;
     sigma = sn;
   }
+  if (pdeg != nullptr)
+    for (int i = max(1, pdeg[k]); i < degree; i++) {
+      ck[3 * i] = 0.0;
+      ck[3 * i + 1] = 0.0;
+      ck[3 * i + 2] = 1.0;
+    }
 }
-void launch_cheb_coeffs(const BatchArgs& b, const double* bounds, double* cheb, int degree, cudaStream_t st) {
-  count_launch(); k_cheb_coeffs<<<(b.M + 127) / 128, 128, 0, st>>>(b, bounds, cheb, degree);
+void launch_cheb_coeffs(const BatchArgs& b, const double* bounds, double* cheb, int degree, cudaStream_t st,
+                        const int* pdeg) {
+  count_launch(); k_cheb_coeffs<<<(b.M + 127) / 128, 128, 0, st>>>(b, bounds, cheb, degree, pdeg);
 }
 
 // Y = alpha (HX - c X) with the step-1 coefficients
@@ -233,30 +242,41 @@ __global__ void k_update_convergence(BatchArgs b, const double* resid2, int ldr,
 // Filter degree of the next pass: the largest m <= max_degree for which the scaled Chebyshev polynomial's
 // growth over the block's spectrum, |T_m(x(a0))| = cosh(m acosh|x(a0)|), stays within range_log
 // (= acosh of the largest growth the precision carries), minimised over the active elements; one CTA.
-__global__ void k_pass_degree(BatchArgs b, const double* bounds, int max_degree, double range_log, int* out) {
+__global__ void k_pass_degree(BatchArgs b, const double* bounds, int max_degree, double range_log, int* pdeg,
+                              int* out) {
   __shared__ int red[256];
-  int m = max_degree;
-  for (int k = threadIdx.x; k < b.M; k += blockDim.x) {
-    if (b.flags && !(b.flags[k] & EF_ACTIVE)) continue;
+  auto cap = [&](int k) {
     const double a0 = bounds[3 * k], bl = bounds[3 * k + 1], bu = bounds[3 * k + 2];
     const double e = 0.5 * (bu - bl), c = 0.5 * (bu + bl);
     const double x = e > 0.0 ? fabs((a0 - c) / e) : 1.0;
+    int m = max_degree;
     if (x > 1.0) {
       const double mk = floor(range_log / acosh(x));
       if (mk < double(m)) m = int(fmax(mk, 8.0));
     }
-  }
+    return min(m, max_degree);
+  };
+  int m = 2;
+  for (int k = threadIdx.x; k < b.M; k += blockDim.x)
+    if (!b.flags || (b.flags[k] & EF_ACTIVE)) m = max(m, cap(k));
   red[threadIdx.x] = m;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] = min(red[threadIdx.x], red[threadIdx.x + o]);
+    if (threadIdx.x < o) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + o]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = min(red[0], max_degree);
+  const int D = red[0];
+  // an element stops after d_k steps with D - d_k even (the frozen recurrence alternates two vectors)
+  for (int k = threadIdx.x; k < b.M; k += blockDim.x) {
+    int dk = (!b.flags || (b.flags[k] & EF_ACTIVE)) ? cap(k) : D;
+    dk -= (D - dk) & 1;
+    pdeg[k] = max(dk, 2);
+  }
+  if (threadIdx.x == 0) *out = D;
 }
-void launch_pass_degree(const BatchArgs& b, const double* bounds, int max_degree, double range_log, int* out,
-                        cudaStream_t st) {
-  count_launch(); k_pass_degree<<<1, 256, 0, st>>>(b, bounds, max_degree, range_log, out);
+void launch_pass_degree(const BatchArgs& b, const double* bounds, int max_degree, double range_log, int* pdeg,
+                        int* out, cudaStream_t st) {
+  count_launch(); k_pass_degree<<<1, 256, 0, st>>>(b, bounds, max_degree, range_log, pdeg, out);
 }
 
 void launch_update_convergence(const BatchArgs& b, const double* resid2, int ldr, double* resid, const double* theta,

@@ -89,7 +89,9 @@ void launch_forward(const HxPlan& pl, const HxArgs& args, const T* X, cplx<T>* S
 template <typename T>
 void launch_zline(const HxPlan& pl, const HxArgs& args, cplx<T>* S, int mult_mode, cudaStream_t st);
 template <typename T>
-void launch_inverse_raw(const HxPlan& pl, const HxArgs& args, const cplx<T>* S, T* Y, cudaStream_t st);
+// inverse transform of a spectrum (unnormalised); deriv = 0 / 1 applies d/dx / d/dy to a spectrum that
+// was transformed along x and y only (the forward plane pass), deriv = -1 nothing
+void launch_inverse_raw(const HxPlan& pl, const HxArgs& args, const cplx<T>* S, T* Y, cudaStream_t st, int deriv = -1);
 
 // ---- batched per-element dense kernels (k_linalg.cu) ----
 struct BatchArgs {
@@ -97,12 +99,21 @@ struct BatchArgs {
   const int* flags;      // may be null
   int M;
 };
+// Gram matrices of FP32 blocks on the tensor cores (3xTF32, k_gram_tc.cu); 0 when the shape is not handled
+int launch_gram_tc(const BatchArgs& b, const float* A, const long long* ao, int na_mode, const float* B,
+                   const long long* bo, int nb_mode, int npts_mode, double* G, int ldg, cudaStream_t st,
+                   double scale, int max_rows);
+// subspace rotation of FP32 blocks on the tensor cores (3xTF32, k_gram_tc.cu); 0 when the shape is not handled
+int launch_rotate_tc(const BatchArgs& b, const float* X, const long long* xo, float* Z, const long long* zo,
+                     int nin_mode, int nout_mode, int npts_mode, const double* W, int ldw, const float* X2, float* Z2,
+                     const double* theta, double* resid2, int ldr, cudaStream_t st, int max_rows);
+int take_tc_error();   // 1 when a bounded tensor-core wait ran out since the last call (clears the flag)
+
 // G_k[i][j] += dV * sum_p A_k[i][p] w(p) B_k[j][p]   (i < na, j < nb; ld = ldg)
 template <typename TI>
 void launch_gram(const BatchArgs& b, const TI* A, const long long* ao, int na_mode, const TI* B, const long long* bo,
                  int nb_mode, int npts_mode, const double* weight, const long long* wo, double* G, int ldg,
                  cudaStream_t st, double scale = 1.0);
-// radial factor tables g of every element's Q boxes (k_fused.cu)
 // Z_k[j][p] = sum_i W_k[i][j] X_k[i][p] (in place allowed), optional second block and residuals
 template <typename TX, typename TZ>
 void launch_rotate(const BatchArgs& b, const TX* X, const long long* xo, TZ* Z, const long long* zo, int nin_mode,
@@ -121,7 +132,9 @@ void launch_random_init(const BatchArgs& b, T* X, const long long* xo, unsigned 
 template <typename T>
 void launch_cheb_first(const BatchArgs& b, const T* X, const T* HX, T* Y, const long long* xo, const double* cheb,
                        int cheb_stride, cudaStream_t st);
-void launch_cheb_coeffs(const BatchArgs& b, const double* bounds, double* cheb, int degree, cudaStream_t st);
+// per-element coefficients of a filter of `degree` steps; with pdeg, element k stops after pdeg[k] steps
+void launch_cheb_coeffs(const BatchArgs& b, const double* bounds, double* cheb, int degree, cudaStream_t st,
+                        const int* pdeg = nullptr);
 template <typename TS, typename TD>
 void launch_convert(const BatchArgs& b, const TS* X, const long long* xo, TD* Y, const long long* yo, int nvec_mode,
                     cudaStream_t st);
@@ -130,8 +143,9 @@ void launch_setup_v(const BatchArgs& b, const AtomBox* boxes, const double* dtab
 void launch_restrict(const BatchArgs& b, const double* X, const long long* xo, double* XE, const long long* eo,
                      int nvec_mode, cudaStream_t st);
 void launch_alb_sign(const BatchArgs& b, double* A, const long long* ao, double* C, int ldc, cudaStream_t st);
-void launch_pass_degree(const BatchArgs& b, const double* bounds, int max_degree, double range_log, int* out,
-                        cudaStream_t st);
+// filter degree of the next pass per element (pdeg) and for the batch (out = max over active elements)
+void launch_pass_degree(const BatchArgs& b, const double* bounds, int max_degree, double range_log, int* pdeg,
+                        int* out, cudaStream_t st);
 void launch_update_convergence(const BatchArgs& b, const double* resid2, int ldr, double* resid, const double* theta,
                                double* bounds, double tol, double tol_mixed, int mixed, double* prev_res,
                                int* stall, int* flags, int* active_count, int* iters, cudaStream_t st);

@@ -104,9 +104,8 @@ extern "C" int dgdft_apply_hamiltonian_noalloc(const dgdft_problem* prob, const 
   const size_t o_dtab = b.take(P.dtab.size() * sizeof(double));
   const size_t o_fat = b.take(std::max<size_t>(1, P.fatoms.size()) * sizeof(FusedAtomRec));
   const size_t nq = size_t(std::max(1, P.n_qboxes));
-  const size_t o_plg = b.take(nq * kProjCap * sizeof(float));
-  const size_t o_plw = b.take(nq * kProjCap * sizeof(unsigned));
-  const size_t o_pln = b.take(nq * sizeof(int));
+  const size_t o_plgw = b.take(nq * kProjCap * sizeof(uint2));
+  const size_t o_pln = b.take(2 * nq * sizeof(int));
   const size_t o_xoff = b.take(P.off[OFF_X].size() * sizeof(long long));
   std::vector<size_t> o_grp(P.hx.groups.size());
   for (size_t i = 0; i < P.hx.groups.size(); i++) o_grp[i] = b.take(P.hx.groups[i].elems.size() * sizeof(int));
@@ -160,8 +159,7 @@ extern "C" int dgdft_apply_hamiltonian_noalloc(const dgdft_problem* prob, const 
   h.n_proj_per_atom = P.n_proj_per_atom;
   h.r_cut = P.r_cut;
   h.fatoms = reinterpret_cast<const FusedAtomRec*>(base + o_fat);
-  h.plist = ProjList{reinterpret_cast<float*>(base + o_plg), reinterpret_cast<unsigned*>(base + o_plw),
-                     reinterpret_cast<int*>(base + o_pln)};
+  h.plist = ProjList{reinterpret_cast<uint2*>(base + o_plgw), reinterpret_cast<int*>(base + o_pln)};
   if (P.n_qboxes > 0) launch_build_proj_lists(h.fatoms, h.dtab, P.n_qboxes, P.r_cut, h.plist, st);
   for (const ShapeGroup& g : P.hx.groups)
     if (!launch_fused_group(g, h, X, Y, nullptr, V32, nullptr, 0, OUT_APPLY, st))

@@ -31,7 +31,7 @@ struct Plan {
   ElemDesc* d_desc = nullptr;
   AtomBox* d_boxes = nullptr;
   double* d_dtab = nullptr;
-  ProjList plist{nullptr, nullptr, nullptr};   // compact projector-point lists of the Q boxes (device)
+  ProjList plist{nullptr, nullptr};   // compact projector-point lists of the Q boxes (device)
   int n_qboxes = 0;                            // the Q boxes come first in `boxes`
   FusedAtomRec* d_fatoms = nullptr;
   long long* d_off[kOffKinds] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

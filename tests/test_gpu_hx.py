@@ -21,6 +21,10 @@ CASES = {
     "slab_proj_small": lambda: make_slab(3, 2, (8, 6, 12), (16, 12, 12), 0.45, 6, 4, 5, r_cut=2.6,
                                          width=0.7, proj_width=0.7),
     "slab_q32x32x48": lambda: make_slab(3, 3, (16, 16, 48), (32, 32, 48), 0.4, 12, 8, 7),
+    # Q shapes whose FP32 step runs on a CTA pair (half spectrum over two CTAs); Q = the whole periodic
+    # box in x and y, so projector boxes wrap around
+    "slab_q40x40x48_pair": lambda: make_slab(2, 2, (20, 20, 48), (40, 40, 48), 0.4, 12, 8, 9),
+    "slab_q40x32x48_pair": lambda: make_slab(2, 2, (20, 16, 48), (40, 32, 48), 0.4, 12, 8, 11),
     "cube_odd_radix": lambda: make_cube(3, n=20, L=9.0, n_wells=4, n_proj=4, En=10, n_eig=6, n_alb=4),
 }
 
