@@ -17,6 +17,46 @@ namespace dgdft {
 
 constexpr int kMaxPlaneAtoms = 160;
 
+// ---- shape groups run side by side ----
+// A batch of several Q shapes (one launch per shape group) runs the groups on kGroupStreams side
+// streams forked from and joined back to the caller's stream, so that small groups and the tails of
+// large ones overlap instead of queueing.  The groups touch disjoint elements.  One set of streams and
+// events per device and host thread.
+constexpr int kGroupStreams = 4;
+struct GroupStreams {
+  int dev = -1;
+  cudaStream_t s[kGroupStreams];
+  cudaEvent_t fork, join[kGroupStreams];
+};
+static thread_local GroupStreams g_group_streams[16];
+
+template <typename F> static void for_groups(const HxPlan& pl, cudaStream_t st, F&& launch) {
+  const int ng = int(pl.groups.size());
+  int dev = 0;
+  cudaGetDevice(&dev);
+  GroupStreams* gs = (ng > 1 && dev >= 0 && dev < 16) ? &g_group_streams[dev] : nullptr;
+  if (gs && gs->dev != dev) {
+    bool ok = cudaEventCreateWithFlags(&gs->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < kGroupStreams && ok; i++)
+      ok = cudaStreamCreateWithFlags(&gs->s[i], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&gs->join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (ok) gs->dev = dev;
+    else gs = nullptr;   // no side streams: the groups run one after another on st
+  }
+  if (!gs) {
+    for (const ShapeGroup& g : pl.groups) launch(g, st);
+    return;
+  }
+  cudaEventRecord(gs->fork, st);
+  const int ns = ng < kGroupStreams ? ng : kGroupStreams;
+  for (int i = 0; i < ns; i++) cudaStreamWaitEvent(gs->s[i], gs->fork, 0);
+  for (int gi = 0; gi < ng; gi++) launch(pl.groups[gi], gs->s[gi % ns]);
+  for (int i = 0; i < ns; i++) {
+    cudaEventRecord(gs->join[i], gs->s[i]);
+    cudaStreamWaitEvent(st, gs->join[i], 0);
+  }
+}
+
 int upload_twiddles(const double2* t64, const float2* t32) {
   if (cudaMemcpyToSymbol(g_tw64, t64, sizeof(double2) * kTwiddleCount) != cudaSuccess) return 1;
   if (cudaMemcpyToSymbol(g_tw32, t32, sizeof(float2) * kTwiddleCount) != cudaSuccess) return 1;
@@ -333,13 +373,13 @@ __global__ void __launch_bounds__(256) k_plane_inverse(HxArgs a, const cplx<T>* 
 template <typename T>
 void launch_hx(const HxPlan& pl, const HxArgs& args, const T* X, T* Y, const T* Yprev, const T* V, cplx<T>* S,
                double* P, const double* cheb, int cheb_stride, int out_mode, int mult_mode, cudaStream_t st) {
-  for (const ShapeGroup& g : pl.groups) {
+  for_groups(pl, st, [&](const ShapeGroup& g, cudaStream_t st) {
     HxArgs a = args;
     a.elems = g.d_elems;
     if constexpr (sizeof(T) == 4) {
       if (mult_mode == MULT_KINETIC && out_mode != OUT_RAW && g.fused_ok &&
           launch_fused_group(g, a, X, Y, Yprev, V, cheb, cheb_stride, out_mode, st))
-        continue;
+        return;
     }
     const int eb = sizeof(T);
     const int smA = plane_smem_bytes(g.qn[0], g.qn[1], eb);
@@ -352,40 +392,40 @@ void launch_hx(const HxPlan& pl, const HxArgs& args, const T* X, T* Y, const T* 
     count_launch(); k_zline<T><<<gB, 256, smB, st>>>(a, S, mult_mode, chunk);
     count_launch(); k_plane_inverse<T><<<gA, 256, smA, st>>>(a, S, X, V, (out_mode == OUT_RAW) ? nullptr : P, Y, Yprev, cheb,
                                               cheb_stride, out_mode);
-  }
+  });
 }
 
 // forward transform only (used by the DG gradients): spectrum of X in S
 template <typename T>
 void launch_forward(const HxPlan& pl, const HxArgs& args, const T* X, cplx<T>* S, cudaStream_t st) {
-  for (const ShapeGroup& g : pl.groups) {
+  for_groups(pl, st, [&](const ShapeGroup& g, cudaStream_t st) {
     HxArgs a = args;
     a.elems = g.d_elems;
     dim3 gA(g.qn[2], g.max_nvec, g.n_elems);
     count_launch(); k_plane_forward<T><<<gA, 256, plane_smem_bytes(g.qn[0], g.qn[1], sizeof(T)), st>>>(a, X, S, nullptr);
-  }
+  });
 }
 
 template <typename T>
 void launch_zline(const HxPlan& pl, const HxArgs& args, cplx<T>* S, int mult_mode, cudaStream_t st) {
-  for (const ShapeGroup& g : pl.groups) {
+  for_groups(pl, st, [&](const ShapeGroup& g, cudaStream_t st) {
     HxArgs a = args;
     a.elems = g.d_elems;
     const int hx = g.qn[0] / 2 + 1;
     dim3 gB((g.qn[1] * hx + g.zchunk - 1) / g.zchunk, g.max_nvec, g.n_elems);
     count_launch(); k_zline<T><<<gB, 256, zline_smem_bytes(g.qn[2], g.zchunk, sizeof(T)), st>>>(a, S, mult_mode, g.zchunk);
-  }
+  });
 }
 
 template <typename T>
 void launch_inverse_raw(const HxPlan& pl, const HxArgs& args, const cplx<T>* S, T* Y, cudaStream_t st, int deriv) {
-  for (const ShapeGroup& g : pl.groups) {
+  for_groups(pl, st, [&](const ShapeGroup& g, cudaStream_t st) {
     HxArgs a = args;
     a.elems = g.d_elems;
     dim3 gA(g.qn[2], g.max_nvec, g.n_elems);
     count_launch(); k_plane_inverse<T><<<gA, 256, plane_smem_bytes(g.qn[0], g.qn[1], sizeof(T)), st>>>(
         a, S, nullptr, nullptr, nullptr, Y, nullptr, nullptr, 0, OUT_RAW, deriv);
-  }
+  });
 }
 
 int set_hx_smem_limits() {

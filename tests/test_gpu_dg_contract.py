@@ -10,7 +10,7 @@
   tests).  The assembled eigenvalues are held to 1e-5 Ha and the block measures to 2e-5 ||H_kk||.
 * The mixed small-slab blocks, rotated into the oracle bases, at that block bound.
 * One live ALB-subspace check on an uneven-batch element of the 40x40x48 shape, whose half spectrum does
-  not fit one CTA (multi-pass FP32 kernels).
+  not fit one CTA (its FP32 steps run on a CTA pair).
 """
 import json
 import os
@@ -133,9 +133,9 @@ def test_dg_blocks_small_slab_mixed(ctx):
     assert np.abs(ev_g - ev_o).max() <= 1e-5
 
 
-def test_uneven_multipass_shape_live_subspace(ctx):
-    """An element of the 40x40x48 shape of the uneven batch (multi-pass FP32 kernels), solved alone on
-    the GPU (mixed) and by the oracle: eigenvalues within 1e-6 Ha, ALB subspace sine within 1e-5."""
+def test_uneven_pair_shape_live_subspace(ctx):
+    """An element of the 40x40x48 shape of the uneven batch (its FP32 steps run on a CTA pair), solved
+    alone on the GPU (mixed) and by the oracle: eigenvalues within 1e-6 Ha, ALB subspace sine within 1e-5."""
     import multiprocessing as mp
     import helpers
     from paper_2003_00407_gb300 import api
