@@ -11,13 +11,18 @@
 // over the CTA's 4096 points carries no further FP32 rounding, and the pair goes to FP64 once.  Two
 // accumulator sets alternate: the sums of one period are folded while the next period's products run.
 //
-// One CTA of 256 threads per (element, chunk of 4096 points).  Per stage of 32 points all threads load
-// the rows of A (and B), split them and store the four operand tiles in the canonical no-swizzle
-// K-major layout (8-row x 16-byte core matrices); one thread issues the 4 K-steps x 3 products of
-// `tcgen05.mma.kind::tf32` (M = 128 rows of A, N = 16 * NH8 rows of B) into a tensor-memory
-// accumulator and commits them to the stage's mbarrier.  Two stages alternate, so loads of stage g + 1
-// overlap the products of stage g.  Every wait is bounded: on time-out the kernel records an error and
-// frees its tensor memory.
+// One CTA of 256 threads per (element, chunk of 4096 points).  Per stage of 32 points all threads split
+// the rows of A (and B) loaded one stage ahead into registers and store the four operand tiles in the
+// canonical no-swizzle K-major layout (8-row x 16-byte core matrices); one thread issues the 4 K-steps x 3
+// products of `tcgen05.mma.kind::tf32` (M = 128 rows of A, N = 16 * NH8 rows of B) into a tensor-memory
+// accumulator and commits them to the stage's mbarrier.  Two shared-memory stages alternate, so the
+// loads of stage g + 1 overlap the products of stage g.  Every wait is bounded: on time-out the kernel
+// records an error and frees its tensor memory.
+//
+// The subspace rotation X W on the same tensor cores (k_rotate_tc) serves the exported
+// dgdft_rotate_fp32; the solver's FP32 stage rotates with the CUDA-core kernel (k_linalg.cu), which
+// measured faster (34 ms against 59 ms per sheet launch: the tensor-core version waits on each tile's
+// loads and products in turn).
 #include <cstdint>
 #include "kernels.h"
 
@@ -193,6 +198,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     fence_before();
   };
   const int nst = (p_end - p_begin + kTcKT - 1) / kTcKT;
+  // thread t stages row i = t % 128 at the K quads h, h + 2, h + 4, h + 6 (h = t / 128) of every stage;
+  // the next stage's loads are issued as soon as this stage's values are in shared memory, so that they
+  // are in flight during the barrier, the products and the folding
+  const int ri = threadIdx.x & 127, rh = threadIdx.x >> 7;
+  const float* Arow = Ak + (long long)ri * np;
+  const float* Brow = Bk + (long long)ri * np;
+  float4 xa[4], xb[4];
+  auto fetch = [&](int g) {
+    const int p0 = p_begin + g * kTcKT;
+#pragma unroll
+    for (int it = 0; it < 4; it++) {
+      const int p = p0 + 4 * (rh + 2 * it);
+      xa[it] = ri < na ? load4(Arow, p, p_end, vecA) : make_float4(0.f, 0.f, 0.f, 0.f);
+      xb[it] = (!same && ri < nb) ? load4(Brow, p, p_end, vecB) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  fetch(0);
   bool ok = true;
   int committed = -1;   // last stage whose products were committed
   for (int g = 0; g < nst; g++) {
@@ -201,13 +223,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // the products of stage g - 2 (same buffers) are complete
     const bool w = g < 2 || mbar_wait(smem_u32(&mbar[buf]), ((g - 2) >> 1) & 1);
     if (!__syncthreads_and(w)) { ok = false; break; }
-    const int p0 = p_begin + g * kTcKT;
-    for (int e = threadIdx.x; e < 128 * (kTcKT / 4); e += kTcThreads) {
-      const int i = e & 127, kq = e >> 7;
-      if (i < na) put4(sb, sb + kTcTile, i, kq, load4(Ak + (long long)i * np, p0 + 4 * kq, p_end, vecA));
-      if (!same && i < nb)
-        put4(sb + 2 * kTcTile, sb + 3 * kTcTile, i, kq, load4(Bk + (long long)i * np, p0 + 4 * kq, p_end, vecB));
+#pragma unroll
+    for (int it = 0; it < 4; it++) {
+      if (ri < na) put4(sb, sb + kTcTile, ri, rh + 2 * it, xa[it]);
+      if (!same && ri < nb) put4(sb + 2 * kTcTile, sb + 3 * kTcTile, ri, rh + 2 * it, xb[it]);
     }
+    if (g + 1 < nst) fetch(g + 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // tiles visible to the tensor cores
     fence_before();
     __syncthreads();

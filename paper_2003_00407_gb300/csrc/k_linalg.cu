@@ -253,12 +253,6 @@ template <typename TX, typename TZ>
 void launch_rotate(const BatchArgs& b, const TX* X, const long long* xo, TZ* Z, const long long* zo, int nin_mode,
                    int nout_mode, int npts_mode, const double* W, int ldw, const TX* X2, TZ* Z2, const double* theta,
                    double* resid2, int ldr, cudaStream_t st) {
-  if constexpr (std::is_same<TX, float>::value && std::is_same<TZ, float>::value) {
-    // FP32 blocks: 3xTF32 on the tensor cores (k_gram_tc.cu)
-    if (launch_rotate_tc(b, X, xo, Z, zo, nin_mode, nout_mode, npts_mode, W, ldw, X2, Z2, theta, resid2, ldr, st,
-                         std::max(g_max_nblk, g_max_nalb)))
-      return;
-  }
   constexpr int Q = rot_q<TX>();
   const int pts = kRotTiles * 16 * Q;
   dim3 grid((g_max_points + pts - 1) / pts, b.M);
