@@ -408,9 +408,9 @@ def filter_roofline(ctx, api, _abi, wl, torch, stream, res):
     ach = bytes_step / t_step / 1e9
     del X
     # DRAM bytes of one full launch: dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of the
-    # same kernel on 16 sheet elements, scaled by the vectors processed (x 64); only for the 1024-element
-    # sheet, which that capture samples
-    traffic = 738.0e6 * (M / 16.0) if M == 1024 and int(np.max(N)) == 49152 else None
+    # same kernel on 16 sheet elements (524.9 MB + 221.9 MB), scaled by the vectors processed (x 64); only
+    # for the 1024-element sheet, which that capture samples
+    traffic = 746.8e6 * (M / 16.0) if M == 1024 and int(np.max(N)) == 49152 else None
     return {"bound": "hbm", "achieved": ach, "peak": peak[0], "unit": "GB/s", "frac": ach / peak[0],
             "traffic": traffic, "kernel": "k_cheb_fused (one FP32 Chebyshev step over all vectors; one launch)",
             "step_ms": 1000 * t_step, "bytes_per_step": bytes_step, "peak_source": peak[1]}

@@ -204,8 +204,9 @@ int dgdft_gram_fp32(dgdft_ctx* ctx, int n_blocks, const int* nx, const int* ny, 
 
 /* Subspace rotation of FP32 vector blocks on the tensor cores: for every block k,
  *   Z_k[j][p] = sum_i W_k[i][j] X_k[i][p]          (j < nout[k], i < nin[k], p < np[k])
- * the X <- X U^-1 step of Cholesky-QR and the X <- X C step of Rayleigh-Ritz of Alg. CheFSI, as the FP32
- * stage of dgdft_alb_generate applies them (the same kernel).  X and W are split into two TF32 parts each
+ * the X <- X U^-1 step of Cholesky-QR and the X <- X C step of Rayleigh-Ritz of Alg. CheFSI, on the
+ * tensor cores (dgdft_alb_generate's FP32 stage applies the same rotations with a CUDA-core kernel, which
+ * measured faster on the sheet elements).  X and W are split into two TF32 parts each
  * (3xTF32 products on tcgen05 tensor cores, FP32 accumulation over the nin terms).  Error: a few 2^-22
  * of sum_i |W_k[i][j]| |X_k[i][p]|.
  *   n_blocks               number of blocks (0: nothing to do)

@@ -24,6 +24,7 @@
 // measured faster (34 ms against 59 ms per sheet launch: the tensor-core version waits on each tile's
 // loads and products in turn).
 #include <cstdint>
+#include <mutex>
 #include "kernels.h"
 
 namespace dgdft {
@@ -463,7 +464,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
-static int tc_attr_done_dev = -1;
+// Kernel attributes are per device: set them once per device (bit per device id < 64), under a lock so
+// that no host thread launches on a device before its attributes are in place.
+static std::mutex g_tc_attr_mutex;
+static unsigned long long g_tc_attr_devs = 0, g_rot_attr_devs = 0;
+template <typename F> static void once_per_device(unsigned long long& devs, F&& set) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_tc_attr_mutex);
+  const unsigned long long bit = (dev >= 0 && dev < 64) ? 1ull << dev : 0ull;
+  if (bit && (devs & bit)) return;
+  set();
+  devs |= bit;
+}
 
 // Gram matrices on the tensor cores for FP32 inputs (callers zero G first).  Returns 0 when the shape is
 // not handled (more than 96 rows in B or 128 in A), so that the caller falls back to the CUDA-core kernel.
@@ -474,17 +487,14 @@ int launch_gram_tc(const BatchArgs& b, const float* A, const long long* ao, int 
   const int nh8 = (max_rows + 15) / 16;
   const int same = (A == B && ao == bo && na_mode == nb_mode) ? 1 : 0;
   const int sm = 2 * (same ? 2 : 4) * kTcTile;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (tc_attr_done_dev != dev) {
+  once_per_device(g_tc_attr_devs, [] {
     cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4 * kTcTile);
     cudaFuncSetAttribute(k_gram_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4 * kTcTile);
     cudaFuncSetAttribute(k_gram_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4 * kTcTile);
     cudaFuncSetAttribute(k_gram_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4 * kTcTile);
     cudaFuncSetAttribute(k_gram_tc<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4 * kTcTile);
     cudaFuncSetAttribute(k_gram_tc<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4 * kTcTile);
-    tc_attr_done_dev = dev;
-  }
+  });
   dim3 grid((g_max_points + kTcChunk - 1) / kTcChunk, b.M);
   count_launch();
   switch (nh8) {
@@ -498,8 +508,6 @@ int launch_gram_tc(const BatchArgs& b, const float* A, const long long* ao, int 
   return 1;
 }
 
-static int rot_attr_done_dev = -1;
-
 // Subspace rotation of FP32 blocks on the tensor cores; 0 when the shape is not handled (more than 96
 // input or output vectors), so that the caller falls back to the CUDA-core kernel.
 int launch_rotate_tc(const BatchArgs& b, const float* X, const long long* xo, float* Z, const long long* zo,
@@ -512,17 +520,14 @@ int launch_rotate_tc(const BatchArgs& b, const float* X, const long long* xo, fl
   const int limit = 200 * 1024;
   const int nbuf = 2 * wbytes + 4 * abytes <= limit ? 2 : 1;
   const int sm = 2 * wbytes + 2 * nbuf * abytes;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (rot_attr_done_dev != dev) {
+  once_per_device(g_rot_attr_devs, [limit] {
     cudaFuncSetAttribute(k_rotate_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
     cudaFuncSetAttribute(k_rotate_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
     cudaFuncSetAttribute(k_rotate_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
     cudaFuncSetAttribute(k_rotate_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
     cudaFuncSetAttribute(k_rotate_tc<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
     cudaFuncSetAttribute(k_rotate_tc<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
-    rot_attr_done_dev = dev;
-  }
+  });
   if (sm > limit) return 0;
   dim3 grid((g_max_points + kRotTcTiles * 128 - 1) / (kRotTcTiles * 128), b.M);
   count_launch();

@@ -21,7 +21,8 @@ constexpr int kMaxPlaneAtoms = 160;
 // A batch of several Q shapes (one launch per shape group) runs the groups on kGroupStreams side
 // streams forked from and joined back to the caller's stream, so that small groups and the tails of
 // large ones overlap instead of queueing.  The groups touch disjoint elements.  One set of streams and
-// events per device and host thread.
+// events per device and host thread, created on first use and kept for the life of the process (no
+// destruction at thread or process exit, when the CUDA context may already be gone).
 constexpr int kGroupStreams = 4;
 struct GroupStreams {
   int dev = -1;
