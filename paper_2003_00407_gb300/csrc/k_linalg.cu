@@ -32,10 +32,12 @@ __device__ __forceinline__ bool elem_active(const BatchArgs& b, int k) {
 // 16 x 16 threads, each owning an R x R register tile of the (16R)^2 outputs; the points
 // stream through shared memory in tiles of kGramKT.  FP64 inputs accumulate in FP64;
 // FP32 inputs accumulate kGramSub points in FP32 registers, then into FP64 accumulators.
+// SYM (B is A, the same rows): only the 16 x 16 blocks on and above the diagonal are formed
+// (R (R + 1) / 2 of the R^2 register blocks), and each one above it is also added at its mirror.
 constexpr int kGramKT = 32;      // points per shared-memory tile
 constexpr int kGramSub = 128;    // points per FP32 partial sum
 constexpr int kGramChunk = 4096; // points per CTA
-template <typename TI, int R>
+template <typename TI, int R, bool SYM>
 __global__ void __launch_bounds__(256) k_gram(BatchArgs b, const TI* __restrict__ A, const long long* ao, int na_mode,
                                               const TI* __restrict__ B, const long long* bo, int nb_mode, int npts_mode,
                                               const double* __restrict__ w, const long long* wo, double* G, int ldg,
@@ -86,7 +88,8 @@ __global__ void __launch_bounds__(256) k_gram(BatchArgs b, const TI* __restrict_
 #pragma unroll
       for (int r = 0; r < R; r++)
 #pragma unroll
-        for (int c = 0; c < R; c++) part[r][c] = fma(av[r], bv[c], part[r][c]);
+        for (int c = 0; c < R; c++)
+          if (!SYM || r <= c) part[r][c] = fma(av[r], bv[c], part[r][c]);
     }
     __syncthreads();
     if (((p0 - p_begin + kGramKT) % kGramSub) == 0 || p0 + kGramKT >= p_end) {
@@ -104,8 +107,12 @@ __global__ void __launch_bounds__(256) k_gram(BatchArgs b, const TI* __restrict_
     if (i >= na) continue;
 #pragma unroll
     for (int c = 0; c < R; c++) {
+      if (SYM && r > c) continue;
       const int j = tx + 16 * c;
-      if (j < nb) atomicAdd(&Gk[i * ldg + j], acc[r][c] * f);
+      if (j < nb) {
+        atomicAdd(&Gk[i * ldg + j], acc[r][c] * f);
+        if (SYM && r < c) atomicAdd(&Gk[j * ldg + i], acc[r][c] * f);
+      }
     }
   }
 }
@@ -126,13 +133,20 @@ void launch_gram(const BatchArgs& b, const TI* A, const long long* ao, int na_mo
   }
   dim3 grid((g_max_points + kGramChunk - 1) / kGramChunk, b.M);
   count_launch();
+  const bool sym = A == B && ao == bo && na_mode == nb_mode;
+#define DGDFT_GRAM(RR)                                                                                            \
+  if (sym) k_gram<TI, RR, true><<<grid, 256, 0, st>>>(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, weight, wo, G, ldg, \
+                                                      scale);                                                     \
+  else k_gram<TI, RR, false><<<grid, 256, 0, st>>>(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, weight, wo, G, ldg,    \
+                                                   scale)
   switch (tile_r(g_max_nblk)) {
-    case 2: k_gram<TI, 2><<<grid, 256, 0, st>>>(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, weight, wo, G, ldg, scale); break;
-    case 3: k_gram<TI, 3><<<grid, 256, 0, st>>>(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, weight, wo, G, ldg, scale); break;
-    case 4: k_gram<TI, 4><<<grid, 256, 0, st>>>(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, weight, wo, G, ldg, scale); break;
-    case 5: k_gram<TI, 5><<<grid, 256, 0, st>>>(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, weight, wo, G, ldg, scale); break;
-    default: k_gram<TI, 6><<<grid, 256, 0, st>>>(b, A, ao, na_mode, B, bo, nb_mode, npts_mode, weight, wo, G, ldg, scale); break;
+    case 2: DGDFT_GRAM(2); break;
+    case 3: DGDFT_GRAM(3); break;
+    case 4: DGDFT_GRAM(4); break;
+    case 5: DGDFT_GRAM(5); break;
+    default: DGDFT_GRAM(6); break;
   }
+#undef DGDFT_GRAM
 }
 thread_local int g_max_points = 0;
 
