@@ -21,8 +21,8 @@
 //
 // The subspace rotation X W on the same tensor cores (k_rotate_tc) serves the exported
 // dgdft_rotate_fp32; the solver's FP32 stage rotates with the CUDA-core kernel (k_linalg.cu), which
-// measured faster (34 ms against 59 ms per sheet launch: the tensor-core version waits on each tile's
-// loads and products in turn).
+// measured faster: a 256-element sheet ALB generation took 7.57 s with it and 7.66 s with k_rotate_tc
+// (loads issued a step ahead; 34 ms against 59 ms per sheet launch before that).
 #include <cstdint>
 #include <mutex>
 #include "kernels.h"
@@ -350,23 +350,36 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   float* Zk = Z ? Z + zo[k] : nullptr;
   float* Z2k = Z2 ? Z2 + zo[k] : nullptr;
 
-  // A tile of step s: X (or X2) rows i < kpad at the tile's 128 points, split, K-major core matrices
-  auto load_step = [&](int s) {
+  // A tile of step s: X (or X2) rows i < kpad at the tile's 128 points, split, K-major core matrices.
+  // Thread t handles point t % 128 of the tile and the input-vector quads t / 128 + 2 it; a step's values
+  // are loaded into registers (fetch) one step before they are split into shared memory (put), so the
+  // loads are in flight during the products and the epilogue of the step before.
+  constexpr int kMaxQ = 12;   // quads per thread at kpad = 96
+  const int pp = threadIdx.x & 127, qh = threadIdx.x >> 7;
+  float4 xq[kMaxQ];
+  auto fetch = [&](int s) {
     const int t = s / nblk, bi = s % nblk;
     const float* src = bi ? X2k : Xk;
+    const int p = pc0 + t * 128 + pp;
+#pragma unroll
+    for (int it = 0; it < kMaxQ; it++) {
+      const int i0 = 4 * (qh + 2 * it);
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i0 < kpad && p < np) {
+        if (i0 < nin) x.x = src[(long long)i0 * np + p];
+        if (i0 + 1 < nin) x.y = src[(long long)(i0 + 1) * np + p];
+        if (i0 + 2 < nin) x.z = src[(long long)(i0 + 2) * np + p];
+        if (i0 + 3 < nin) x.w = src[(long long)(i0 + 3) * np + p];
+      }
+      xq[it] = x;
+    }
+  };
+  auto put = [&](int s) {
     unsigned char* ah = sA + (s % nbuf) * 2 * abytes;
     unsigned char* al = ah + abytes;
-    const int p0 = pc0 + t * 128;
-    for (int e = threadIdx.x; e < (kpad / 4) * 128; e += kTcThreads) {
-      const int pp = e & 127, i4 = e >> 7;
-      const int p = p0 + pp;
-      float4 x;
-      x.x = (4 * i4 < nin && p < np) ? src[(long long)(4 * i4) * np + p] : 0.f;
-      x.y = (4 * i4 + 1 < nin && p < np) ? src[(long long)(4 * i4 + 1) * np + p] : 0.f;
-      x.z = (4 * i4 + 2 < nin && p < np) ? src[(long long)(4 * i4 + 2) * np + p] : 0.f;
-      x.w = (4 * i4 + 3 < nin && p < np) ? src[(long long)(4 * i4 + 3) * np + p] : 0.f;
-      put4(ah, al, pp, i4, x);
-    }
+#pragma unroll
+    for (int it = 0; it < kMaxQ; it++)
+      if (4 * (qh + 2 * it) < kpad) put4(ah, al, pp, qh + 2 * it, xq[it]);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   };
   auto issue_step = [&](int s) {   // one thread
@@ -389,7 +402,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tmem = tmem_slot;
   bool ok = true;
   int committed = -1, known_done = -1;   // last committed step; last step whose products were waited for
-  load_step(0);
+  fetch(0);
+  put(0);
   fence_before();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -397,6 +411,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     issue_step(0);
   }
   committed = 0;
+  if (nstep > 1) fetch(1);
   for (int s = 0; s < nstep && ok; s++) {
     if (s + 1 < nstep) {
       // the buffer of step s + 1 was last read by the products of step s + 1 - nbuf
@@ -404,7 +419,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const bool w = prev <= known_done || mbar_wait(smem_u32(&mbar[prev % nbuf]), (prev / nbuf) & 1);
       if (!__syncthreads_and(w)) { ok = false; break; }
       known_done = max(known_done, prev);
-      load_step(s + 1);
+      put(s + 1);
+      if (s + 2 < nstep) fetch(s + 2);
     }
     fence_before();
     __syncthreads();
